@@ -1,0 +1,198 @@
+/*
+ * inpc_rast.h -- C ABI of the GB300 tiled point rasterizer.
+ *
+ * The rasterizer of "A Bag of Tricks for Efficient Implicit Neural Point
+ * Clouds" (arXiv 2508.19140): N points (position p_i, opacity o_i, an
+ * n_w-channel feature f_i; Sec. 2 "Rendering Feature Maps") are projected
+ * through a pinhole camera, splatted as bilinear 2x2 footprints or as small
+ * isotropic Gaussians (Sec. 3.2 "Rendering Points as Small Gaussians"), binned
+ * into 16x16 tiles and sorted by (tile, depth, point index) (Sec. 3.2 "Tiled
+ * Rendering", split sort), then alpha-blended front to back by Eq. 1 into a
+ * feature image F (H x W x n_w), an alpha image and a depth image. The
+ * backward pass implements the corrected gradient of the appendix (Eq. 2,
+ * "Addressing Gradient Approximations"), fragments with alpha = 0 included.
+ *
+ * Conventions
+ *   - All pointers inside the structs below are DEVICE pointers owned by the
+ *     caller unless stated otherwise; the library never allocates, frees or
+ *     retains them beyond the call. The `rast_*_t` structs themselves live in
+ *     host memory and are read during the call only.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Compute entry points enqueue work and return without a host
+ *     synchronisation; argument errors are reported synchronously.
+ *   - Camera: x_c = R x_w + t (R row-major), u = fx x_c / z_c + cx,
+ *     v = fy y_c / z_c + cy; pixel (i, j) has its centre at (i + 1/2, j + 1/2).
+ *     Points with z_c <= near_z or z_c >= far_z are culled.
+ *   - Layouts: xyz [n][3] f32, opacity [n] f32, scale [n] f32, feat [n][C]
+ *     f32 or bf16 (row-major), images [H][W][C] f32 (HWC, as F in Sec. 2),
+ *     alpha and depth [H][W] f32.
+ *   - Errors: no C++ exception crosses this ABI and no kernel traps. A
+ *     device-side capacity overflow is recorded in the workspace and reported
+ *     by rasterize_get_status().
+ */
+#ifndef INPC_RAST_H
+#define INPC_RAST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RAST_OK = 0,
+    RAST_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, bad enum) */
+    RAST_ERR_CAPACITY = 2,       /* workspace too small, or copies exceeded max_copies */
+    RAST_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    RAST_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up */
+    RAST_ERR_NOT_SUPPORTED = 5   /* channel count, tile size or mode not compiled in */
+} rast_status_t;
+
+typedef enum { RAST_SPLAT_BILINEAR = 0, RAST_SPLAT_GAUSSIAN = 1 } rast_mode_t;
+
+/* EWA: Sigma_2D = s^2 J J^T + dilation I with J the affine (Jacobian)
+ * approximation of the perspective projection (Sec. 3.2, small Gaussians).
+ * ISO_SCREEN: Sigma_2D = (s^2 fx fy / z^2 + dilation) I. */
+typedef enum { RAST_GAUSS_EWA = 0, RAST_GAUSS_ISO_SCREEN = 1 } rast_gauss_cov_t;
+
+typedef enum { RAST_F32 = 0, RAST_BF16 = 1 } rast_dtype_t;
+
+typedef enum { RAST_PASS_FWD = 1, RAST_PASS_BWD = 2 } rast_pass_t;
+
+typedef struct {
+    float fx, fy, cx, cy;
+    float R[9];          /* world -> camera rotation, row-major */
+    float t[3];
+    float near_z, far_z;
+    int32_t width, height;
+} rast_camera_t;
+
+typedef struct {
+    int64_t n;             /* number of points (>= 0) */
+    const float* xyz;      /* [n][3] */
+    const float* opacity;  /* [n] */
+    const void* feat;      /* [n][channels], element type feat_dtype */
+    int32_t feat_dtype;    /* rast_dtype_t */
+    int32_t channels;      /* C: 1, 2, 3, 4, 8 or 16 */
+    const float* scale;    /* [n] world-space Gaussian scale; NULL: 5 px at the near plane */
+} rast_points_t;
+
+typedef struct {
+    int32_t mode;          /* rast_mode_t */
+    int32_t gauss_cov;     /* rast_gauss_cov_t */
+    int32_t tile;          /* tile edge in pixels: 16 */
+    int32_t blend_depth;   /* records staged per blend batch: 0 = default (256) */
+    float t_min;           /* early termination: stop before T (1 - a) < t_min (1e-4) */
+    float alpha_max;       /* alpha clamp (0.99) */
+    float dilation;        /* screen-space dilation variance, Gaussian mode (0.16) */
+    int32_t max_copies;    /* capacity: point-tile copies per point (0 = 4 bilinear, 16 Gaussian) */
+    int32_t flags;         /* reserved, 0 */
+} rast_opts_t;
+
+typedef struct {
+    float* feat;    /* [H][W][C] out */
+    float* alpha;   /* [H][W] out: 1 - T_final; may be NULL */
+    float* depth;   /* [H][W] out: sum_i T_i a_i z_i; may be NULL */
+} rast_images_t;
+
+typedef struct {
+    const float* g_feat;   /* [H][W][C] dL/dF (required for BWD) */
+    const float* g_alpha;  /* [H][W] dL/dalpha, NULL = 0 */
+    const float* g_depth;  /* [H][W] dL/ddepth, NULL = 0 */
+    float* d_feat;         /* [n][C] out, f32 whatever feat_dtype is */
+    float* d_opacity;      /* [n] out */
+    float* d_xyz;          /* [n][3] out, Gaussian mode only (NULL allowed) */
+    float* d_scale;        /* [n] out, Gaussian mode with scale != NULL (NULL allowed) */
+} rast_grads_t;
+
+typedef struct {
+    rast_points_t pts;
+    rast_camera_t cam;
+    rast_images_t out;
+    rast_grads_t grad;     /* read by BWD only */
+} rast_view_t;
+
+/* Counters read back by rasterize_get_status(). */
+typedef struct {
+    int32_t status;          /* rast_status_t recorded on the device */
+    int32_t n_views;
+    int64_t n_points;        /* total points over all views */
+    int64_t n_copies;        /* D: point-tile copies created by the last forward */
+    int64_t copy_capacity;   /* copies the workspace can hold */
+    int64_t needed_records;  /* records the blend had to read (after early termination) */
+    int64_t n_tiles;
+    int64_t n_pixels;
+} rast_stats_t;
+
+/* One row of the per-stage timing profile. */
+typedef struct {
+    char name[32];
+    int32_t launches;
+    double total_ms;
+} rast_profile_entry_t;
+
+/* Fill `opts` with the defaults stated above. */
+void rast_default_opts(rast_opts_t* opts);
+
+/* Bytes of device workspace rasterize_batch() needs for these views and
+ * options (0 on invalid arguments). The workspace carries the forward's state
+ * (records, sorted tile lists, per-pixel final T and last contributor) to the
+ * backward pass, so one workspace must outlive the fwd/bwd pair. */
+size_t rasterize_workspace_size(const rast_view_t* views, int32_t n_views, const rast_opts_t* opts);
+
+/* Forward pass of ONE view (Eq. 1): projection + footprint count, split
+ * radix sort by (tile, depth, index), tile ranges, front-to-back blend.
+ * Writes out->feat, out->alpha, out->depth. Equivalent to rasterize_batch
+ * with one view and RAST_PASS_FWD. */
+rast_status_t rasterize_fwd(const rast_points_t* pts, const rast_camera_t* cam,
+                            const rast_opts_t* opts, void* workspace, size_t ws_bytes,
+                            const rast_images_t* out, void* stream);
+
+/* Backward pass of ONE view (appendix Eq. 2, corrected). `workspace` must
+ * hold the state of the matching rasterize_fwd on the same inputs. Writes
+ * every element of the d_* outputs given (zeros for culled points). */
+rast_status_t rasterize_bwd(const rast_points_t* pts, const rast_camera_t* cam,
+                            const rast_opts_t* opts, void* workspace, size_t ws_bytes,
+                            const rast_grads_t* grads, void* stream);
+
+/* Several views (each with its own points, camera, outputs and gradients)
+ * in one launch sequence: global tile ids concatenate the views' tiles, so
+ * one sort and one blend launch serve all views. pass = RAST_PASS_FWD,
+ * RAST_PASS_BWD or both OR-ed. No host synchronisation: capturable in a CUDA
+ * graph. n_views <= 16. */
+rast_status_t rasterize_batch(const rast_view_t* views, int32_t n_views, int32_t pass,
+                              const rast_opts_t* opts, void* workspace, size_t ws_bytes,
+                              void* stream);
+
+/* Synchronises `stream`, then reads the device-side status word and counters
+ * of `workspace` (stats may be NULL). Returns the recorded status. */
+rast_status_t rasterize_get_status(const void* workspace, size_t ws_bytes, void* stream,
+                                   rast_stats_t* stats);
+
+/* Human-readable name of a status code (static storage). */
+const char* rasterize_status_string(rast_status_t status);
+
+/* Byte offsets of the workspace arrays, for inspection by tests:
+ * names "records", "rect", "count", "sorted_vals", "sorted_keys", "ranges",
+ * "t_final", "last", "header"; writes up to `max` (name, offset, bytes)
+ * triples and returns how many exist. Layout only: no device access. */
+typedef struct { char name[24]; int64_t offset; int64_t bytes; } rast_ws_entry_t;
+int32_t rasterize_workspace_layout(const rast_view_t* views, int32_t n_views,
+                                   const rast_opts_t* opts, rast_ws_entry_t* out, int32_t max);
+
+/* Per-stage timing with CUDA events recorded on the launch stream around each
+ * stage. enable(1) clears and starts recording, enable(0) stops. read()
+ * waits for the recorded events, writes up to `max` entries and returns how
+ * many stages were seen. */
+void rasterize_profile_enable(int32_t on);
+int32_t rasterize_profile_read(rast_profile_entry_t* out, int32_t max);
+
+/* Library version string. */
+const char* rasterize_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INPC_RAST_H */

@@ -1,0 +1,513 @@
+// C ABI of the tiled point rasterizer (declared in include/inpc_rast.h).
+//
+// Host side only: argument checks, the workspace layout, the view table the
+// kernels receive by value, and the order of the stages. No stage
+// synchronises with the host, so a whole rasterize_batch call can be captured
+// in a CUDA graph.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rast_internal.cuh"
+
+namespace rast {
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+uint32_t f32_bits(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u;
+}
+
+int bit_length(uint64_t x) {
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+enum Slot {
+    S_HDR, S_REC, S_RECT, S_CNT, S_KEYA0, S_KEYA1, S_VALA0, S_VALA1, S_RECTS, S_BASE, S_BLK,
+    S_KEYC0, S_KEYC1, S_VALC0, S_VALC1, S_PARTIAL, S_HIST, S_BINTOT, S_RANGES, S_CUTOFF,
+    S_TFINAL, S_LAST, S_COUNT
+};
+const char* kSlotNames[S_COUNT] = {
+    "header", "records", "rect", "count", "keys_a0", "keys_a1", "vals_a0", "vals_a1",
+    "rect_sorted", "base", "block_sums", "keys_c0", "keys_c1", "vals_c0", "vals_c1",
+    "partial", "hist", "bin_total", "ranges", "cutoff", "t_final", "last"};
+
+struct Plan {
+    ViewTable vt;
+    size_t off[S_COUNT];
+    size_t bytes[S_COUNT];
+    size_t total;
+    int64_t copy_cap, hist_tiles, blk_cap;
+    SortPlan planA, planC;
+    int partial_floats;
+};
+
+rast_status_t check_view(const rast_view_t& v, int pass) {
+    const rast_points_t& p = v.pts;
+    const rast_camera_t& c = v.cam;
+    if (p.n < 0) return RAST_ERR_ARG;
+    if (p.n > 0 && (!p.xyz || !p.opacity || !p.feat)) return RAST_ERR_ARG;
+    if (c.width < 1 || c.height < 1 || c.width > 65535 * kTile || c.height > 65535 * kTile)
+        return RAST_ERR_ARG;
+    if (!(c.near_z > 0.f) || !(c.far_z > c.near_z) || !std::isfinite(c.far_z)) return RAST_ERR_ARG;
+    const float* cf = &c.fx;
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(cf[k])) return RAST_ERR_ARG;
+    if ((pass & RAST_PASS_FWD) && !v.out.feat) return RAST_ERR_ARG;
+    if ((pass & RAST_PASS_BWD) && !v.grad.g_feat) return RAST_ERR_ARG;
+    return RAST_OK;
+}
+
+rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_opts_t* o, int pass,
+                        Plan& pl) {
+    if (!views || !o || n_views < 1 || n_views > kMaxViews) return RAST_ERR_ARG;
+    if (o->mode != RAST_SPLAT_BILINEAR && o->mode != RAST_SPLAT_GAUSSIAN) return RAST_ERR_ARG;
+    if (o->gauss_cov != RAST_GAUSS_EWA && o->gauss_cov != RAST_GAUSS_ISO_SCREEN) return RAST_ERR_ARG;
+    if (o->tile != kTile) return RAST_ERR_NOT_SUPPORTED;
+    if (o->blend_depth != 0 && o->blend_depth != kBatch) return RAST_ERR_NOT_SUPPORTED;
+    if (!(o->t_min >= 0.f) || !(o->alpha_max > 0.f && o->alpha_max < 1.f)) return RAST_ERR_ARG;
+    if (!(o->dilation >= 0.f) || o->max_copies < 0) return RAST_ERR_ARG;
+    const int C = views[0].pts.channels;
+    const int dt = views[0].pts.feat_dtype;
+    if (dt != RAST_F32 && dt != RAST_BF16) return RAST_ERR_ARG;
+    if (C < 1) return RAST_ERR_ARG;
+    if (!channels_supported(C)) return RAST_ERR_NOT_SUPPORTED;
+    std::memset(&pl, 0, sizeof(pl));
+    ViewTable& vt = pl.vt;
+    vt.n_views = n_views;
+    vt.C = C;
+    vt.bf16 = dt == RAST_BF16;
+    vt.mode = o->mode;
+    vt.gauss_cov = o->gauss_cov;
+    vt.t_min = o->t_min;
+    vt.alpha_max = o->alpha_max;
+    vt.dilation = o->dilation;
+    vt.feat_word = o->mode == RAST_SPLAT_GAUSSIAN ? 8 : 4;
+    const int fwords = vt.bf16 ? (C + 1) / 2 : C;
+    vt.rec_words = (vt.feat_word + fwords + 3) / 4 * 4;
+    int64_t npt = 0, ntile = 0, npix = 0;
+    uint32_t max_cull = 1;
+    for (int k = 0; k < n_views; ++k) {
+        const rast_view_t& v = views[k];
+        if (v.pts.channels != C || v.pts.feat_dtype != dt) return RAST_ERR_ARG;
+        rast_status_t st = check_view(v, pass);
+        if (st != RAST_OK) return st;
+        ViewDev& d = vt.v[k];
+        const rast_camera_t& c = v.cam;
+        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+        for (int j = 0; j < 9; ++j) d.R[j] = c.R[j];
+        for (int j = 0; j < 3; ++j) d.t[j] = c.t[j];
+        d.near_z = c.near_z;
+        d.far_z = c.far_z;
+        d.W = c.width;
+        d.H = c.height;
+        d.tiles_x = (c.width + kTile - 1) / kTile;
+        d.tiles_y = (c.height + kTile - 1) / kTile;
+        d.key_base = f32_bits(c.near_z);
+        d.key_cull = f32_bits(c.far_z) - f32_bits(c.near_z);
+        if (d.key_cull > max_cull) max_cull = d.key_cull;
+        d.pt_off = npt;
+        d.n = v.pts.n;
+        d.tile_off = ntile;
+        d.pix_off = npix;
+        d.xyz = v.pts.xyz;
+        d.opacity = v.pts.opacity;
+        d.feat = v.pts.feat;
+        d.scale = v.pts.scale;
+        d.out_feat = v.out.feat;
+        d.out_alpha = v.out.alpha;
+        d.out_depth = v.out.depth;
+        d.g_feat = v.grad.g_feat;
+        d.g_alpha = v.grad.g_alpha;
+        d.g_depth = v.grad.g_depth;
+        d.d_feat = v.grad.d_feat;
+        d.d_opacity = v.grad.d_opacity;
+        d.d_xyz = v.grad.d_xyz;
+        d.d_scale = v.grad.d_scale;
+        npt += v.pts.n;
+        ntile += (int64_t)d.tiles_x * d.tiles_y;
+        npix += (int64_t)c.width * c.height;
+    }
+    if (npt >= ((int64_t)1 << 31) || ntile >= ((int64_t)1 << 31) || npix >= ((int64_t)1 << 40))
+        return RAST_ERR_ARG;
+    vt.n_total = npt;
+    vt.tiles_total = ntile;
+    vt.pix_total = npix;
+
+    const int64_t per_pt = o->max_copies > 0 ? o->max_copies : (o->mode == RAST_SPLAT_BILINEAR ? 4 : 16);
+    pl.copy_cap = npt * per_pt;
+    if (pl.copy_cap >= ((int64_t)1 << 32)) pl.copy_cap = ((int64_t)1 << 32) - 1;
+    pl.hist_tiles = sort_hist_tiles(npt > pl.copy_cap ? npt : pl.copy_cap);
+    pl.blk_cap = (npt + kScanItems - 1) / kScanItems + 1;
+    pl.planA = make_sort_plan(bit_length(max_cull));
+    pl.planC = make_sort_plan(bit_length((uint64_t)(ntile > 0 ? ntile - 1 : 0)));
+    pl.partial_floats = o->mode == RAST_SPLAT_BILINEAR ? C + 1 : C + 7;
+
+    const int64_t N = npt, D = pl.copy_cap;
+    pl.bytes[S_HDR] = sizeof(WsHeader);
+    pl.bytes[S_REC] = (size_t)N * vt.rec_words * 4;
+    pl.bytes[S_RECT] = (size_t)N * 8;
+    pl.bytes[S_CNT] = (size_t)N * 4;
+    pl.bytes[S_KEYA0] = pl.bytes[S_KEYA1] = pl.bytes[S_VALA0] = pl.bytes[S_VALA1] = (size_t)N * 4;
+    pl.bytes[S_RECTS] = (size_t)N * 8;
+    pl.bytes[S_BASE] = (size_t)N * 4;
+    pl.bytes[S_BLK] = (size_t)pl.blk_cap * 4;
+    pl.bytes[S_KEYC0] = pl.bytes[S_KEYC1] = pl.bytes[S_VALC0] = pl.bytes[S_VALC1] = (size_t)D * 4;
+    pl.bytes[S_PARTIAL] = (size_t)D * pl.partial_floats * 4;
+    pl.bytes[S_HIST] = (size_t)512 * pl.hist_tiles * 4;
+    pl.bytes[S_BINTOT] = (size_t)512 * 8 * 4;
+    pl.bytes[S_RANGES] = (size_t)ntile * 8;
+    pl.bytes[S_CUTOFF] = (size_t)ntile * 8;
+    pl.bytes[S_TFINAL] = (size_t)npix * 4;
+    pl.bytes[S_LAST] = (size_t)npix * 4;
+    size_t off = 0;
+    for (int k = 0; k < S_COUNT; ++k) {
+        pl.off[k] = off;
+        off += align_up(pl.bytes[k] ? pl.bytes[k] : 1);
+    }
+    pl.total = off;
+    return RAST_OK;
+}
+
+Bufs make_bufs(const Plan& pl, void* ws) {
+    char* w = static_cast<char*>(ws);
+    auto at = [&](int s) { return (void*)(w + pl.off[s]); };
+    Bufs b;
+    std::memset(&b, 0, sizeof(b));
+    b.hdr = (WsHeader*)at(S_HDR);
+    b.rec = (uint32_t*)at(S_REC);
+    b.rect = (uint2*)at(S_RECT);
+    b.cnt = (uint32_t*)at(S_CNT);
+    b.keyA[0] = (uint32_t*)at(S_KEYA0);
+    b.keyA[1] = (uint32_t*)at(S_KEYA1);
+    b.valA[0] = (uint32_t*)at(S_VALA0);
+    b.valA[1] = (uint32_t*)at(S_VALA1);
+    b.rectS = (uint2*)at(S_RECTS);
+    b.base = (uint32_t*)at(S_BASE);
+    b.blk = (uint32_t*)at(S_BLK);
+    b.keyC[0] = (uint32_t*)at(S_KEYC0);
+    b.keyC[1] = (uint32_t*)at(S_KEYC1);
+    b.valC[0] = (uint32_t*)at(S_VALC0);
+    b.valC[1] = (uint32_t*)at(S_VALC1);
+    b.partial = (float*)at(S_PARTIAL);
+    b.hist = (uint32_t*)at(S_HIST);
+    b.bin_total = (uint32_t*)at(S_BINTOT);
+    b.ranges = (uint2*)at(S_RANGES);
+    b.cutoff = (uint2*)at(S_CUTOFF);
+    b.t_final = (float*)at(S_TFINAL);
+    b.last = (uint32_t*)at(S_LAST);
+    b.copy_cap = pl.copy_cap;
+    b.hist_tiles = pl.hist_tiles;
+    b.blk_cap = pl.blk_cap;
+    return b;
+}
+
+__global__ void k_init_header(WsHeader* h, int32_t n_views, long long n_points, long long cap,
+                              long long n_tiles, long long n_pixels) {
+    h->error = 0u;
+    h->n_copies = 0u;
+    h->n_copies_raw = 0u;
+    h->n_views = (uint32_t)n_views;
+    h->needed = 0ull;
+    h->n_points = n_points;
+    h->copy_cap = cap;
+    h->n_tiles = n_tiles;
+    h->n_pixels = n_pixels;
+}
+
+// ---- per-stage profiling ---------------------------------------------------
+
+struct ProfRec {
+    std::string name;
+    cudaEvent_t a, b;
+};
+
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+Profiler g_prof;
+
+struct Stage {
+    cudaStream_t s;
+    int idx = -1;
+    Stage(const char* name, cudaStream_t st) : s(st) {
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        if (!g_prof.on) return;
+        ProfRec r{name, g_prof.get(), g_prof.get()};
+        cudaEventRecord(r.a, s);
+        g_prof.recs.push_back(r);
+        idx = (int)g_prof.recs.size() - 1;
+    }
+    ~Stage() {
+        if (idx < 0) return;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        if (idx < (int)g_prof.recs.size()) cudaEventRecord(g_prof.recs[idx].b, s);
+    }
+};
+
+#define RAST_TRY(expr)                      \
+    do {                                    \
+        cudaError_t e_ = (expr);            \
+        if (e_ != cudaSuccess) return e_;   \
+    } while (0)
+
+cudaError_t run_fwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
+    const ViewTable& vt = pl.vt;
+    {
+        Stage st("init", s);
+        k_init_header<<<1, 1, 0, s>>>(b.hdr, vt.n_views, vt.n_total, pl.copy_cap, vt.tiles_total,
+                                      vt.pix_total);
+        RAST_TRY(cudaGetLastError());
+    }
+    {
+        Stage st("project", s);
+        RAST_TRY(launch_project(vt, b, s));
+    }
+    int ra = 0, rc = 0;
+    {
+        Stage st("sort_depth", s);
+        uint32_t* k[2] = {b.keyA[0], b.keyA[1]};
+        uint32_t* v[2] = {b.valA[0], b.valA[1]};
+        RAST_TRY(radix_sort(k, v, vt.n_total, nullptr, vt.n_total, pl.planA, b.hist, b.hist_tiles,
+                            b.bin_total, s, &ra));
+    }
+    const uint32_t* depth_sorted = b.valA[ra];
+    {
+        Stage st("duplicate", s);
+        RAST_TRY(launch_duplicate(vt, b, depth_sorted, s));
+    }
+    {
+        Stage st("sort_tile", s);
+        uint32_t* k[2] = {b.keyC[0], b.keyC[1]};
+        uint32_t* v[2] = {b.valC[0], b.valC[1]};
+        RAST_TRY(radix_sort(k, v, 0, &b.hdr->n_copies, pl.copy_cap, pl.planC, b.hist, b.hist_tiles,
+                            b.bin_total, s, &rc));
+    }
+    {
+        Stage st("ranges", s);
+        RAST_TRY(launch_ranges(vt, b, b.keyC[rc], s));
+    }
+    {
+        Stage st("blend_fwd", s);
+        RAST_TRY(launch_blend_fwd(vt, b, b.valC[rc], s));
+    }
+    return cudaSuccess;
+}
+
+cudaError_t run_bwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
+    const ViewTable& vt = pl.vt;
+    const int rc = pl.planC.passes & 1;
+    {
+        Stage st("point_scan", s);
+        RAST_TRY(launch_point_scan(vt, b, s));
+    }
+    {
+        Stage st("blend_bwd", s);
+        RAST_TRY(launch_blend_bwd(vt, b, b.valC[rc], s));
+    }
+    {
+        Stage st("reduce_grads", s);
+        RAST_TRY(launch_reduce_grads(vt, b, s));
+    }
+    return cudaSuccess;
+}
+
+rast_view_t single_view(const rast_points_t* pts, const rast_camera_t* cam, const rast_images_t* out,
+                        const rast_grads_t* grads) {
+    rast_view_t v;
+    std::memset(&v, 0, sizeof(v));
+    v.pts = *pts;
+    v.cam = *cam;
+    if (out) v.out = *out;
+    if (grads) v.grad = *grads;
+    return v;
+}
+
+}  // namespace
+}  // namespace rast
+
+using namespace rast;
+
+extern "C" {
+
+void rast_default_opts(rast_opts_t* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->mode = RAST_SPLAT_BILINEAR;
+    o->gauss_cov = RAST_GAUSS_EWA;
+    o->tile = kTile;
+    o->blend_depth = 0;
+    o->t_min = 1e-4f;
+    o->alpha_max = 0.99f;
+    o->dilation = 0.16f;
+    o->max_copies = 0;
+    o->flags = 0;
+}
+
+size_t rasterize_workspace_size(const rast_view_t* views, int32_t n_views, const rast_opts_t* opts) {
+    Plan pl;
+    if (make_plan(views, n_views, opts, 0, pl) != RAST_OK) return 0;
+    return pl.total;
+}
+
+int32_t rasterize_workspace_layout(const rast_view_t* views, int32_t n_views, const rast_opts_t* opts,
+                                   rast_ws_entry_t* out, int32_t max) {
+    Plan pl;
+    if (make_plan(views, n_views, opts, 0, pl) != RAST_OK) return -1;
+    const int ra = pl.planA.passes & 1, rc = pl.planC.passes & 1;
+    struct Alias { const char* name; int slot; };
+    const Alias extra[] = {{"depth_sorted", ra ? S_VALA1 : S_VALA0},
+                           {"sorted_keys", rc ? S_KEYC1 : S_KEYC0},
+                           {"sorted_vals", rc ? S_VALC1 : S_VALC0}};
+    int n = 0;
+    for (int k = 0; k < S_COUNT; ++k, ++n) {
+        if (out && n < max) {
+            std::snprintf(out[n].name, sizeof(out[n].name), "%s", kSlotNames[k]);
+            out[n].offset = (int64_t)pl.off[k];
+            out[n].bytes = (int64_t)pl.bytes[k];
+        }
+    }
+    for (const Alias& a : extra) {
+        if (out && n < max) {
+            std::snprintf(out[n].name, sizeof(out[n].name), "%s", a.name);
+            out[n].offset = (int64_t)pl.off[a.slot];
+            out[n].bytes = (int64_t)pl.bytes[a.slot];
+        }
+        ++n;
+    }
+    return n;
+}
+
+rast_status_t rasterize_batch(const rast_view_t* views, int32_t n_views, int32_t pass,
+                              const rast_opts_t* opts, void* workspace, size_t ws_bytes,
+                              void* stream) {
+    if (pass < 1 || pass > 3) return RAST_ERR_ARG;
+    Plan pl;
+    const rast_status_t st = make_plan(views, n_views, opts, pass, pl);
+    if (st != RAST_OK) return st;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return RAST_ERR_ARG;
+    if (ws_bytes < pl.total) return RAST_ERR_CAPACITY;
+    const Bufs b = make_bufs(pl, workspace);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (pass & RAST_PASS_FWD) {
+        if (run_fwd(pl, b, s) != cudaSuccess) return RAST_ERR_CUDA;
+    }
+    if (pass & RAST_PASS_BWD) {
+        if (run_bwd(pl, b, s) != cudaSuccess) return RAST_ERR_CUDA;
+    }
+    return RAST_OK;
+}
+
+rast_status_t rasterize_fwd(const rast_points_t* pts, const rast_camera_t* cam, const rast_opts_t* opts,
+                            void* workspace, size_t ws_bytes, const rast_images_t* out, void* stream) {
+    if (!pts || !cam || !out) return RAST_ERR_ARG;
+    const rast_view_t v = single_view(pts, cam, out, nullptr);
+    return rasterize_batch(&v, 1, RAST_PASS_FWD, opts, workspace, ws_bytes, stream);
+}
+
+rast_status_t rasterize_bwd(const rast_points_t* pts, const rast_camera_t* cam, const rast_opts_t* opts,
+                            void* workspace, size_t ws_bytes, const rast_grads_t* grads, void* stream) {
+    if (!pts || !cam || !grads) return RAST_ERR_ARG;
+    const rast_view_t v = single_view(pts, cam, nullptr, grads);
+    return rasterize_batch(&v, 1, RAST_PASS_BWD, opts, workspace, ws_bytes, stream);
+}
+
+rast_status_t rasterize_get_status(const void* workspace, size_t ws_bytes, void* stream,
+                                   rast_stats_t* stats) {
+    if (!workspace || ws_bytes < sizeof(WsHeader)) return RAST_ERR_ARG;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return RAST_ERR_CUDA;
+    WsHeader h;
+    if (cudaMemcpy(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return RAST_ERR_CUDA;
+    rast_status_t r = RAST_OK;
+    if (h.error & kErrCapacity) r = RAST_ERR_CAPACITY;
+    else if (h.error & kErrTimeout) r = RAST_ERR_TIMEOUT;
+    if (stats) {
+        stats->status = r;
+        stats->n_views = (int32_t)h.n_views;
+        stats->n_points = h.n_points;
+        stats->n_copies = h.n_copies_raw;
+        stats->copy_capacity = h.copy_cap;
+        stats->needed_records = (int64_t)h.needed;
+        stats->n_tiles = h.n_tiles;
+        stats->n_pixels = h.n_pixels;
+    }
+    return r;
+}
+
+const char* rasterize_status_string(rast_status_t s) {
+    switch (s) {
+        case RAST_OK: return "ok";
+        case RAST_ERR_ARG: return "invalid argument";
+        case RAST_ERR_CAPACITY: return "capacity exceeded";
+        case RAST_ERR_CUDA: return "CUDA error";
+        case RAST_ERR_TIMEOUT: return "device wait timed out";
+        case RAST_ERR_NOT_SUPPORTED: return "not supported";
+    }
+    return "unknown status";
+}
+
+void rasterize_profile_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (auto& r : g_prof.recs) {
+        g_prof.pool.push_back(r.a);
+        g_prof.pool.push_back(r.b);
+    }
+    g_prof.recs.clear();
+    g_prof.on = on != 0;
+}
+
+int32_t rasterize_profile_read(rast_profile_entry_t* out, int32_t max) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    std::vector<rast_profile_entry_t> agg;
+    for (auto& r : g_prof.recs) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) ms = 0.f;
+        rast_profile_entry_t* e = nullptr;
+        for (auto& x : agg)
+            if (r.name == x.name) e = &x;
+        if (!e) {
+            rast_profile_entry_t z;
+            std::memset(&z, 0, sizeof(z));
+            std::snprintf(z.name, sizeof(z.name), "%s", r.name.c_str());
+            agg.push_back(z);
+            e = &agg.back();
+        }
+        e->launches += 1;
+        e->total_ms += ms;
+    }
+    const int n = (int)agg.size();
+    for (int k = 0; k < n && k < max; ++k) out[k] = agg[k];
+    return n;
+}
+
+const char* rasterize_version(void) { return "inpc-rast-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,541 @@
+// K7 + K8: backward pass (appendix, corrected Eq. 2).
+//
+// K7 replays each tile's list back to front, per pixel, from the saved final
+// transmittance T_{K+1} and the position of the last blended fragment:
+//   T_k     = T_{k+1} / (1 - a_k)
+//   dL/da_k = T_k (g_F . f_k + g_D z_k) - (S_k + g_D SD_k - g_A T_{K+1}) / (1 - a_k)
+//   S_k     = sum_{i>k} a_i T_i (g_F . f_i),  SD_k = sum_{i>k} a_i T_i z_i
+//   dL/df_k = T_k a_k g_F,  dL/dz_k = T_k a_k g_D,
+// where g_A is dL/dalpha of the alpha output 1 - T_{K+1} (the background term
+// of Eq. 2 arrives through it). Fragments with a_k = 0 are not skipped.
+// Chain: bilinear dL/do = w dL/da; Gaussian dL/do = G dL/da and, through
+// G = exp(-m/2), dL/d(u, v) and dL/d(conic); nothing flows through a clamped
+// alpha. The FP32 alpha of every fragment is recomputed with the forward's
+// exact operations.
+//
+// Determinism without float atomics: the contributions of all pixels of a tile
+// to one copy are combined in a fixed order inside the CTA (bilinear: the copy
+// owns four slots, one per pixel of its 2x2 box; Gaussian: one slot per warp,
+// filled by a fixed-order shuffle reduction), and written to the copy's own
+// slot base[i] + (rank of the tile in the point's tile rect). K8 then sums a
+// point's slots in rect order. A per-tile cutoff (depth bits and point index of
+// the last record the replay touched) tells K8 which slots were written.
+#include "blend_common.cuh"
+
+namespace rast {
+namespace {
+
+__device__ __forceinline__ uint32_t rect_rank(uint2 r, int tx, int ty) {
+    const int tx0 = r.x & 0xffff, ty0 = r.x >> 16, tx1 = r.y & 0xffff;
+    return (uint32_t)((ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0));
+}
+
+__device__ __forceinline__ uint32_t block_max_u32(uint32_t x, uint32_t* s) {
+    if (threadIdx.x == 0) *s = 0;
+    __syncthreads();
+    atomicMax(s, x);
+    __syncthreads();
+    const uint32_t r = *s;
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------- bilinear
+
+template <int C, bool BF16>
+__global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
+    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pts,
+    const uint32_t* __restrict__ rec, const float* __restrict__ t_final,
+    const uint32_t* __restrict__ last_in, const uint32_t* __restrict__ base,
+    const uint2* __restrict__ rect, float* __restrict__ partial, uint2* __restrict__ cutoff) {
+    constexpr int P = C + 1;  // dfeat[C], dopacity
+    __shared__ float s_a[kBatch], s_b[kBatch], s_o[kBatch], s_z[kBatch];
+    __shared__ int s_i0[kBatch], s_j0[kBatch];
+    __shared__ float s_f[C][kBatch];
+    __shared__ uint32_t s_mask[kTilePix][9];
+    extern __shared__ float s_contrib[];  // [4 slots][P][kBatch]
+    __shared__ uint32_t s_red;
+
+    const int64_t tile = blockIdx.x;
+    const ViewDev& V = vt.v[view_of_tile(vt, tile)];
+    const int64_t lt = tile - V.tile_off;
+    const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
+    const bool inside = px < V.W && py < V.H;
+    const uint2 rg = ranges[tile];
+    const int RW = vt.rec_words, FW = vt.feat_word;
+    const float amax = vt.alpha_max;
+
+    float T = 1.f, Tfin = 1.f, gA = 0.f, gD = 0.f;
+    float gF[C];
+    uint32_t last = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) gF[c] = 0.f;
+    if (inside) {
+        const int64_t pix = (int64_t)py * V.W + px;
+        T = Tfin = t_final[V.pix_off + pix];
+        last = last_in[V.pix_off + pix];
+#pragma unroll
+        for (int c = 0; c < C; ++c) gF[c] = V.g_feat[pix * C + c];
+        if (V.g_alpha) gA = V.g_alpha[pix];
+        if (V.g_depth) gD = V.g_depth[pix];
+    }
+    const uint32_t maxlast = block_max_u32(last, &s_red);
+    if (maxlast == 0) {
+        if (tid == 0) cutoff[tile] = make_uint2(0u, 0u);
+        return;
+    }
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
+    float Sg = 0.f, SD = 0.f;
+    const float Kd = -gA * Tfin;  // constant part of the 1/(1-a) term
+
+    for (int bi = (int)((maxlast - 1) / kBatch); bi >= 0; --bi) {
+        const uint32_t rel0 = (uint32_t)bi * kBatch;
+        const uint32_t b0 = rg.x + rel0;
+        const uint32_t bend = rg.x + maxlast < b0 + kBatch ? rg.x + maxlast : b0 + kBatch;
+        const uint32_t q = b0 + tid;
+#pragma unroll
+        for (int k = 0; k < 4 * P; ++k) s_contrib[k * kBatch + tid] = 0.f;
+        uint32_t gi = 0;
+        if (q < bend) {
+            gi = pts[q];
+            const uint32_t* rp = rec + (size_t)gi * RW;
+            const uint4 g = *reinterpret_cast<const uint4*>(rp);
+            float f[C];
+            load_features<C, BF16>(rp + FW, f);
+            const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
+            s_a[tid] = bg.a;
+            s_b[tid] = bg.b;
+            s_o[tid] = __uint_as_float(g.w);
+            s_z[tid] = __uint_as_float(g.z);
+            s_i0[tid] = bg.i0;
+            s_j0[tid] = bg.j0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) s_f[c][tid] = f[c];
+            const int X0 = bg.i0 - tx * kTile, Y0 = bg.j0 - ty * kTile;
+            const uint32_t bit = 1u << lane;
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                const int Y = Y0 + dy;
+                if ((unsigned)Y >= (unsigned)kTile) continue;
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int X = X0 + dx;
+                    if ((unsigned)X < (unsigned)kTile) atomicOr(&s_mask[Y * kTile + X][warp], bit);
+                }
+            }
+            if (q + 1 == rg.x + maxlast) cutoff[tile] = make_uint2(g.z, gi);
+        }
+        __syncthreads();
+        if (inside && last > rel0) {
+#pragma unroll 1
+            for (int w = 7; w >= 0; --w) {
+                uint32_t m = s_mask[tid][w];
+                while (m) {
+                    const int bit = 31 - __clz(m);
+                    m &= ~(1u << bit);
+                    const int r = w * 32 + bit;
+                    if (rel0 + r >= last) continue;
+                    const int i0 = s_i0[r], j0 = s_j0[r];
+                    const float wgt = bilin_weight(px, py, i0, j0, s_a[r], s_b[r]);
+                    const float ow = __fmul_rn(s_o[r], wgt);
+                    const float alpha = fminf(ow, amax);
+                    const float om = __fsub_rn(1.f, alpha);
+                    const float Tk = __fdiv_rn(T, om);
+                    float fdot = 0.f;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], s_f[c][r], fdot);
+                    const float z = s_z[r];
+                    const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) / om;
+                    const float ta = Tk * alpha;
+                    Sg = fmaf(ta, fdot, Sg);
+                    SD = fmaf(ta, z, SD);
+                    T = Tk;
+                    const int slot = (px - i0) + 2 * (py - j0);
+                    float* cb = s_contrib + (slot * P) * kBatch + r;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) cb[c * kBatch] = ta * gF[c];
+                    cb[C * kBatch] = (ow <= amax) ? wgt * dalpha : 0.f;
+                }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
+        __syncthreads();
+        if (q < bend) {
+            const uint2 rc = rect[gi];
+            float* out = partial + (size_t)(base[gi] + rect_rank(rc, tx, ty)) * P;
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const float* cb = s_contrib + k * kBatch + tid;
+                out[k] = ((cb[0] + cb[P * kBatch]) + cb[2 * P * kBatch]) + cb[3 * P * kBatch];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- Gaussian
+
+constexpr int kGBatch = 128;  // records per backward batch (shared-memory bound)
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+template <int C, bool BF16>
+__global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
+    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pts,
+    const uint32_t* __restrict__ rec, const float* __restrict__ t_final,
+    const uint32_t* __restrict__ last_in, const uint32_t* __restrict__ base,
+    const uint2* __restrict__ rect, float* __restrict__ partial, uint2* __restrict__ cutoff) {
+    constexpr int P = C + 7;  // dfeat[C], do, du, dv, dca, dcb, dcc, dz
+    __shared__ float s_um[kGBatch], s_vm[kGBatch], s_o[kGBatch], s_z[kGBatch];
+    __shared__ float s_ca[kGBatch], s_cb[kGBatch], s_cc[kGBatch];
+    __shared__ int4 s_box[kGBatch];
+    __shared__ float s_f[C][kGBatch];
+    extern __shared__ float s_contrib[];  // [8 warps][P][kGBatch]
+    __shared__ uint32_t s_red;
+
+    const int64_t tile = blockIdx.x;
+    const ViewDev& V = vt.v[view_of_tile(vt, tile)];
+    const int64_t lt = tile - V.tile_off;
+    const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sx0 = tx * kTile + (warp & 1) * 8, sy0 = ty * kTile + (warp >> 1) * 4;
+    const int px = sx0 + (lane & 7), py = sy0 + (lane >> 3);
+    const bool inside = px < V.W && py < V.H;
+    const uint2 rg = ranges[tile];
+    const int RW = vt.rec_words, FW = vt.feat_word;
+    const float amax = vt.alpha_max;
+    const float fpx = (float)px, fpy = (float)py;
+
+    float T = 1.f, Tfin = 1.f, gA = 0.f, gD = 0.f;
+    float gF[C];
+    uint32_t last = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) gF[c] = 0.f;
+    if (inside) {
+        const int64_t pix = (int64_t)py * V.W + px;
+        T = Tfin = t_final[V.pix_off + pix];
+        last = last_in[V.pix_off + pix];
+#pragma unroll
+        for (int c = 0; c < C; ++c) gF[c] = V.g_feat[pix * C + c];
+        if (V.g_alpha) gA = V.g_alpha[pix];
+        if (V.g_depth) gD = V.g_depth[pix];
+    }
+    const uint32_t maxlast = block_max_u32(last, &s_red);
+    if (maxlast == 0) {
+        if (tid == 0) cutoff[tile] = make_uint2(0u, 0u);
+        return;
+    }
+    float Sg = 0.f, SD = 0.f;
+    const float Kd = -gA * Tfin;
+
+    for (int bi = (int)((maxlast - 1) / kGBatch); bi >= 0; --bi) {
+        const uint32_t rel0 = (uint32_t)bi * kGBatch;
+        const uint32_t b0 = rg.x + rel0;
+        const uint32_t bend = rg.x + maxlast < b0 + kGBatch ? rg.x + maxlast : b0 + kGBatch;
+        const int nrec = (int)(bend - b0);
+        for (int k = tid; k < 8 * P * kGBatch; k += kBlendThreads) s_contrib[k] = 0.f;
+        uint32_t gi = 0;
+        const uint32_t q = b0 + tid;
+        if (tid < kGBatch && q < bend) {
+            gi = pts[q];
+            const uint32_t* rp = rec + (size_t)gi * RW;
+            const uint4 g = *reinterpret_cast<const uint4*>(rp);
+            const uint4 h = *reinterpret_cast<const uint4*>(rp + 4);
+            float f[C];
+            load_features<C, BF16>(rp + FW, f);
+            const float um = __fsub_rn(__uint_as_float(g.x), 0.5f);
+            const float vm = __fsub_rn(__uint_as_float(g.y), 0.5f);
+            const GaussBox bx = gauss_box(um, vm, __uint_as_float(h.w));
+            s_um[tid] = um;
+            s_vm[tid] = vm;
+            s_z[tid] = __uint_as_float(g.z);
+            s_o[tid] = __uint_as_float(g.w);
+            s_ca[tid] = __uint_as_float(h.x);
+            s_cb[tid] = __uint_as_float(h.y);
+            s_cc[tid] = __uint_as_float(h.z);
+            s_box[tid] = make_int4(bx.x0, bx.x1, bx.y0, bx.y1);
+#pragma unroll
+            for (int c = 0; c < C; ++c) s_f[c][tid] = f[c];
+            if (q + 1 == rg.x + maxlast) cutoff[tile] = make_uint2(g.z, gi);
+        }
+        __syncthreads();
+        const uint32_t wmax = __reduce_max_sync(0xffffffffu, last);
+        if (wmax > rel0) {
+#pragma unroll 1
+            for (int grp = (nrec - 1) / 32; grp >= 0; --grp) {
+                const int r0 = grp * 32;
+                bool hit = false;
+                if (r0 + lane < nrec) {
+                    const int4 bb = s_box[r0 + lane];
+                    hit = bb.x <= sx0 + 7 && bb.y >= sx0 && bb.z <= sy0 + 3 && bb.w >= sy0;
+                }
+                uint32_t m = __ballot_sync(0xffffffffu, hit);
+                while (m) {
+                    const int bit = 31 - __clz(m);
+                    m &= ~(1u << bit);
+                    const int r = r0 + bit;
+                    float v[P];
+#pragma unroll
+                    for (int k = 0; k < P; ++k) v[k] = 0.f;
+                    bool act = inside && rel0 + r < last;
+                    if (act) {
+                        const int4 bb = s_box[r];
+                        act = px >= bb.x && px <= bb.y && py >= bb.z && py <= bb.w;
+                    }
+                    float dx = 0.f, dy = 0.f, mm = 0.f;
+                    if (act) {
+                        dx = __fsub_rn(fpx, s_um[r]);
+                        dy = __fsub_rn(fpy, s_vm[r]);
+                        mm = gauss_m(dx, dy, s_ca[r], s_cb[r], s_cc[r]);
+                        act = mm <= 9.f;
+                    }
+                    if (act) {
+                        const float G = gauss_value(mm);
+                        const float o = s_o[r];
+                        const float og = __fmul_rn(o, G);
+                        const float alpha = fminf(og, amax);
+                        const float om = __fsub_rn(1.f, alpha);
+                        const float Tk = __fdiv_rn(T, om);
+                        float fdot = 0.f;
+#pragma unroll
+                        for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], s_f[c][r], fdot);
+                        const float z = s_z[r];
+                        const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) / om;
+                        const float ta = Tk * alpha;
+                        Sg = fmaf(ta, fdot, Sg);
+                        SD = fmaf(ta, z, SD);
+                        T = Tk;
+#pragma unroll
+                        for (int c = 0; c < C; ++c) v[c] = ta * gF[c];
+                        v[C + 6] = ta * gD;
+                        if (og <= amax) {
+                            const float ca = s_ca[r], cbv = s_cb[r], cc = s_cc[r];
+                            const float dm = -0.5f * o * G * dalpha;
+                            v[C] = G * dalpha;
+                            v[C + 1] = -dm * (2.f * ca * dx + 2.f * cbv * dy);
+                            v[C + 2] = -dm * (2.f * cbv * dx + 2.f * cc * dy);
+                            v[C + 3] = dm * dx * dx;
+                            v[C + 4] = dm * 2.f * dx * dy;
+                            v[C + 5] = dm * dy * dy;
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < P; ++k) v[k] = warp_sum(v[k]);
+                    if (lane == 0) {
+#pragma unroll
+                        for (int k = 0; k < P; ++k) s_contrib[(warp * P + k) * kGBatch + r] = v[k];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < kGBatch && q < bend) {
+            const uint2 rc = rect[gi];
+            float* out = partial + (size_t)(base[gi] + rect_rank(rc, tx, ty)) * P;
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                float acc = 0.f;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) acc += s_contrib[(w * P + k) * kGBatch + tid];
+                out[k] = acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- K8 reduce
+
+template <int C, int MODE>
+__global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const uint32_t* __restrict__ rec,
+                                                      const uint2* __restrict__ rect,
+                                                      const uint32_t* __restrict__ base,
+                                                      const uint2* __restrict__ cutoff,
+                                                      const float* __restrict__ partial) {
+    constexpr int P = MODE == 0 ? C + 1 : C + 7;
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= vt.n_total) return;
+    const ViewDev& V = vt.v[view_of_point(vt, gi)];
+    const int64_t i = gi - V.pt_off;
+    float acc[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) acc[k] = 0.f;
+    const uint2 rc = rect[gi];
+    const uint32_t cnt = rect_count(rc);
+    if (cnt) {
+        const uint32_t zb = rec[(size_t)gi * vt.rec_words + 2];
+        const int tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff, ty1 = rc.y >> 16;
+        const float* pp = partial + (size_t)base[gi] * P;
+        int k = 0;
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx, ++k) {
+                const uint2 co = cutoff[V.tile_off + (int64_t)ty * V.tiles_x + tx];
+                const bool done = zb < co.x || (zb == co.x && (uint32_t)gi <= co.y);
+                if (!done) continue;
+#pragma unroll
+                for (int j = 0; j < P; ++j) acc[j] += pp[(size_t)k * P + j];
+            }
+    }
+    if (V.d_feat) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) V.d_feat[i * C + c] = acc[c];
+    }
+    if (V.d_opacity) V.d_opacity[i] = acc[C];
+    if (MODE == 0) {
+        if (V.d_xyz) {
+            V.d_xyz[3 * i] = 0.f;
+            V.d_xyz[3 * i + 1] = 0.f;
+            V.d_xyz[3 * i + 2] = 0.f;
+        }
+        if (V.d_scale) V.d_scale[i] = 0.f;
+        return;
+    }
+    float gx = 0.f, gy = 0.f, gz = 0.f, gs = 0.f;
+    if (cnt) {
+        // Camera-space position (same operation order as the projection).
+        const float x = V.xyz[3 * i], y = V.xyz[3 * i + 1], zw = V.xyz[3 * i + 2];
+        float xc = __fmul_rn(V.R[0], x);
+        xc = __fadd_rn(xc, __fmul_rn(V.R[1], y));
+        xc = __fadd_rn(xc, __fmul_rn(V.R[2], zw));
+        xc = __fadd_rn(xc, V.t[0]);
+        float yc = __fmul_rn(V.R[3], x);
+        yc = __fadd_rn(yc, __fmul_rn(V.R[4], y));
+        yc = __fadd_rn(yc, __fmul_rn(V.R[5], zw));
+        yc = __fadd_rn(yc, V.t[1]);
+        float zc = __fmul_rn(V.R[6], x);
+        zc = __fadd_rn(zc, __fmul_rn(V.R[7], y));
+        zc = __fadd_rn(zc, __fmul_rn(V.R[8], zw));
+        zc = __fadd_rn(zc, V.t[2]);
+        const float fx = V.fx, fy = V.fy;
+        const float s = V.scale ? V.scale[i] : __fdiv_rn(__fmul_rn(5.f, V.near_z), fx);
+        const float s2 = s * s;
+        const float iz = 1.f / zc, iz2 = iz * iz, iz3 = iz2 * iz, iz4 = iz2 * iz2, iz5 = iz4 * iz;
+        float S00, S01, S11;
+        if (vt.gauss_cov == 0) {
+            S00 = s2 * (fx * fx * iz2 + fx * fx * xc * xc * iz4) + vt.dilation;
+            S01 = s2 * (fx * fy * xc * yc * iz4);
+            S11 = s2 * (fy * fy * iz2 + fy * fy * yc * yc * iz4) + vt.dilation;
+        } else {
+            S00 = s2 * fx * fy * iz2 + vt.dilation;
+            S11 = S00;
+            S01 = 0.f;
+        }
+        const float det = S00 * S11 - S01 * S01;
+        const float idet = 1.f / det, idet2 = idet * idet;
+        const float dca = acc[C + 3], dcb = acc[C + 4], dcc = acc[C + 5];
+        // conic a = S11/det, b = -S01/det, c = S00/det
+        const float dS00 = dca * (-S11 * S11 * idet2) + dcb * (S01 * S11 * idet2) +
+                           dcc * (idet - S00 * S11 * idet2);
+        const float dS11 = dca * (idet - S11 * S00 * idet2) + dcb * (S01 * S00 * idet2) +
+                           dcc * (-S00 * S00 * idet2);
+        const float dS01 = dca * (2.f * S11 * S01 * idet2) + dcb * (-idet - 2.f * S01 * S01 * idet2) +
+                           dcc * (2.f * S00 * S01 * idet2);
+        const float du = acc[C + 1], dv = acc[C + 2];
+        gx = du * fx * iz;
+        gy = dv * fy * iz;
+        gz = acc[C + 6] - du * fx * xc * iz2 - dv * fy * yc * iz2;
+        if (vt.gauss_cov == 0) {
+            gx += dS00 * s2 * fx * fx * 2.f * xc * iz4 + dS01 * s2 * fx * fy * yc * iz4;
+            gy += dS11 * s2 * fy * fy * 2.f * yc * iz4 + dS01 * s2 * fx * fy * xc * iz4;
+            gz += dS00 * s2 * (-2.f * fx * fx * iz3 - 4.f * fx * fx * xc * xc * iz5) +
+                  dS11 * s2 * (-2.f * fy * fy * iz3 - 4.f * fy * fy * yc * yc * iz5) +
+                  dS01 * s2 * (-4.f * fx * fy * xc * yc * iz5);
+            gs = dS00 * 2.f * s * (fx * fx * iz2 + fx * fx * xc * xc * iz4) +
+                 dS11 * 2.f * s * (fy * fy * iz2 + fy * fy * yc * yc * iz4) +
+                 dS01 * 2.f * s * (fx * fy * xc * yc * iz4);
+        } else {
+            const float dS = dS00 + dS11;
+            gz += dS * s2 * fx * fy * (-2.f * iz3);
+            gs = dS * 2.f * s * fx * fy * iz2;
+        }
+    }
+    if (V.d_xyz) {
+        const float* R = V.R;
+        V.d_xyz[3 * i + 0] = R[0] * gx + R[3] * gy + R[6] * gz;
+        V.d_xyz[3 * i + 1] = R[1] * gx + R[4] * gy + R[7] * gz;
+        V.d_xyz[3 * i + 2] = R[2] * gx + R[5] * gy + R[8] * gz;
+    }
+    if (V.d_scale) V.d_scale[i] = V.scale ? gs : 0.f;
+}
+
+template <int C, bool BF16>
+cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    const unsigned grid = (unsigned)vt.tiles_total;
+    if (vt.mode == 0) {
+        constexpr size_t smem = sizeof(float) * 4 * (C + 1) * kBatch;
+        static bool set = false;
+        if (!set) {
+            cudaError_t e = cudaFuncSetAttribute(k_blend_bwd_bilinear<C, BF16>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            set = true;
+        }
+        k_blend_bwd_bilinear<C, BF16><<<grid, kBlendThreads, smem, s>>>(
+            vt, b.ranges, pts, b.rec, b.t_final, b.last, b.base, b.rect, b.partial, b.cutoff);
+    } else {
+        constexpr size_t smem = sizeof(float) * 8 * (C + 7) * kGBatch;
+        static bool set = false;
+        if (!set) {
+            cudaError_t e = cudaFuncSetAttribute(k_blend_bwd_gauss<C, BF16>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            set = true;
+        }
+        k_blend_bwd_gauss<C, BF16><<<grid, kBlendThreads, smem, s>>>(
+            vt, b.ranges, pts, b.rec, b.t_final, b.last, b.base, b.rect, b.partial, b.cutoff);
+    }
+    return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t launch_bwd_c(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    return vt.bf16 ? launch_bwd_t<C, true>(vt, b, pts, s) : launch_bwd_t<C, false>(vt, b, pts, s);
+}
+
+template <int C>
+cudaError_t launch_reduce_c(const ViewTable& vt, const Bufs& b, cudaStream_t s) {
+    const unsigned grid = (unsigned)((vt.n_total + 255) / 256);
+    if (vt.mode == 0)
+        k_reduce_grads<C, 0><<<grid, 256, 0, s>>>(vt, b.rec, b.rect, b.base, b.cutoff, b.partial);
+    else
+        k_reduce_grads<C, 1><<<grid, 256, 0, s>>>(vt, b.rec, b.rect, b.base, b.cutoff, b.partial);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_blend_bwd(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    if (vt.tiles_total == 0) return cudaSuccess;
+    switch (vt.C) {
+        case 1: return launch_bwd_c<1>(vt, b, pts, s);
+        case 2: return launch_bwd_c<2>(vt, b, pts, s);
+        case 3: return launch_bwd_c<3>(vt, b, pts, s);
+        case 4: return launch_bwd_c<4>(vt, b, pts, s);
+        case 8: return launch_bwd_c<8>(vt, b, pts, s);
+        case 16: return launch_bwd_c<16>(vt, b, pts, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_reduce_grads(const ViewTable& vt, const Bufs& b, cudaStream_t s) {
+    if (vt.n_total == 0) return cudaSuccess;
+    switch (vt.C) {
+        case 1: return launch_reduce_c<1>(vt, b, s);
+        case 2: return launch_reduce_c<2>(vt, b, s);
+        case 3: return launch_reduce_c<3>(vt, b, s);
+        case 4: return launch_reduce_c<4>(vt, b, s);
+        case 8: return launch_reduce_c<8>(vt, b, s);
+        case 16: return launch_reduce_c<16>(vt, b, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rast

@@ -1,0 +1,107 @@
+// Shared pieces of the blend kernels (K6 forward, K7 backward).
+//
+// A record is gathered once per (tile, batch) by one thread and staged in
+// shared memory; the per-pixel work then reads only shared memory. The
+// per-fragment alpha and the coverage test are single device functions used
+// by both passes, so the backward replays the forward's FP32 decisions bit for
+// bit (round-to-nearest intrinsics, no contraction):
+//   bilinear:  a = (u - 1/2) - floor(u - 1/2), w = wx * wy with wx = 1 - a at
+//              the anchor column and a at the next one, alpha = min(o w, amax);
+//   Gaussian:  d = (px - (u - 1/2), py - (v - 1/2)),
+//              m = ((a dx) dx + 2 (b dx) dy) + (c dy) dy, covered iff the pixel
+//              is in the box of radius r and m <= 9, alpha = min(o exp(-m/2), amax);
+//   step:      T' = T (1 - alpha); the fragment is excluded and the pixel stops
+//              once T' < t_min.
+#pragma once
+
+#include "rast_internal.cuh"
+
+namespace rast {
+
+// Features of one record as FP32 registers.
+template <int C, bool BF16>
+__device__ __forceinline__ void load_features(const uint32_t* __restrict__ rp, float (&f)[C]) {
+    if (!BF16) {
+        if (C % 4 == 0) {
+#pragma unroll
+            for (int c = 0; c < C; c += 4) {
+                const uint4 q = *reinterpret_cast<const uint4*>(rp + c);
+                f[c] = __uint_as_float(q.x);
+                f[c + 1] = __uint_as_float(q.y);
+                f[c + 2] = __uint_as_float(q.z);
+                f[c + 3] = __uint_as_float(q.w);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) f[c] = __uint_as_float(rp[c]);
+        }
+    } else {
+        if (C % 8 == 0) {
+#pragma unroll
+            for (int c = 0; c < C; c += 8) {
+                const uint4 q = *reinterpret_cast<const uint4*>(rp + c / 2);
+                f[c] = bf16lo(q.x); f[c + 1] = bf16hi(q.x);
+                f[c + 2] = bf16lo(q.y); f[c + 3] = bf16hi(q.y);
+                f[c + 4] = bf16lo(q.z); f[c + 5] = bf16hi(q.z);
+                f[c + 6] = bf16lo(q.w); f[c + 7] = bf16hi(q.w);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; c += 2) {
+                const uint32_t w = rp[c / 2];
+                f[c] = bf16lo(w);
+                if (c + 1 < C) f[c + 1] = bf16hi(w);
+            }
+        }
+    }
+}
+
+// Bilinear anchor and fractions from the screen position (exact in FP32).
+struct BilinGeom {
+    int i0, j0;
+    float a, b;
+};
+
+__device__ __forceinline__ BilinGeom bilin_geom(float u, float v) {
+    const float um = __fsub_rn(u, 0.5f), vm = __fsub_rn(v, 0.5f);
+    const float fi = floorf(um), fj = floorf(vm);
+    BilinGeom g;
+    g.i0 = (int)fi;
+    g.j0 = (int)fj;
+    g.a = __fsub_rn(um, fi);
+    g.b = __fsub_rn(vm, fj);
+    return g;
+}
+
+// Bilinear weight of the fragment at pixel (px, py) (a pixel of the 2x2 box).
+__device__ __forceinline__ float bilin_weight(int px, int py, int i0, int j0, float a, float b) {
+    const float wx = (px == i0) ? __fsub_rn(1.f, a) : a;
+    const float wy = (py == j0) ? __fsub_rn(1.f, b) : b;
+    return __fmul_rn(wx, wy);
+}
+
+// Gaussian pixel box from the record's radius r (inclusive, unclipped).
+struct GaussBox {
+    int x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ GaussBox gauss_box(float um, float vm, float r) {
+    GaussBox bx;
+    bx.x0 = (int)ceilf(__fsub_rn(um, r));
+    bx.x1 = (int)floorf(__fadd_rn(um, r));
+    bx.y0 = (int)ceilf(__fsub_rn(vm, r));
+    bx.y1 = (int)floorf(__fadd_rn(vm, r));
+    return bx;
+}
+
+// Mahalanobis distance squared of pixel (px, py) (FP32, fixed order).
+__device__ __forceinline__ float gauss_m(float dx, float dy, float ca, float cb, float cc) {
+    const float t0 = __fmul_rn(__fmul_rn(ca, dx), dx);
+    const float t1 = __fmul_rn(__fmul_rn(cb, dx), dy);
+    const float t2 = __fmul_rn(__fmul_rn(cc, dy), dy);
+    return __fadd_rn(__fadd_rn(t0, __fadd_rn(t1, t1)), t2);
+}
+
+__device__ __forceinline__ float gauss_value(float m) { return expf(__fmul_rn(-0.5f, m)); }
+
+}  // namespace rast

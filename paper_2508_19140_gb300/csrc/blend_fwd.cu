@@ -1,0 +1,301 @@
+// K6: front-to-back blend per 16x16 tile (Eq. 1), one CTA per tile, one
+// thread per pixel.
+//
+// F = sum_i T_i a_i f_i, T_i = prod_{j<i} (1 - a_j), over the pixel's covering
+// fragments in (depth, point index) order, stopping before the first fragment
+// that would take T below t_min. Each CTA walks its tile's sorted list in
+// batches of 256 records: every thread gathers one record (two or three
+// 128-bit loads of a 16-byte aligned record) into shared memory, then each
+// pixel composites the records of the batch that cover it, in list order.
+//
+// Bilinear splats touch at most 4 pixels, so testing every record against
+// every pixel (256 tests per record) would make the kernel ALU-bound. Instead
+// the record's thread sets one bit per covered pixel in a per-pixel 256-bit
+// mask (shared-memory atomicOr, order-free and therefore deterministic), and
+// each pixel visits only its set bits in ascending order = list order.
+//
+// Gaussian splats cover many pixels; there each warp owns an 8x4 sub-tile,
+// ballots the batch's records whose pixel box overlaps the sub-tile, and
+// composites only those, all 32 lanes in lockstep.
+//
+// The CTA stops reading as soon as every in-image pixel has terminated
+// (__syncthreads_count), which is where early termination saves HBM traffic.
+// Saved for the backward pass: T_final and the 1-based list position of the
+// last blended fragment per pixel. The per-tile count of records the method had
+// to read (every record if some pixel never terminated, else up to the last
+// terminating fragment) is summed into the workspace header.
+#include "blend_common.cuh"
+
+namespace rast {
+namespace {
+
+template <int C, bool BF16>
+__global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
+    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pts,
+    const uint32_t* __restrict__ rec, float* __restrict__ t_final, uint32_t* __restrict__ last_out,
+    WsHeader* __restrict__ hdr) {
+    __shared__ float s_a[kBatch], s_b[kBatch], s_o[kBatch], s_z[kBatch];
+    __shared__ int s_i0[kBatch], s_j0[kBatch];
+    __shared__ float s_f[C][kBatch];
+    __shared__ uint32_t s_mask[kTilePix][9];  // 8 words + 1 pad: conflict-free row reads
+    __shared__ uint32_t s_maxstop;
+
+    const int64_t tile = blockIdx.x;
+    const ViewDev& V = vt.v[view_of_tile(vt, tile)];
+    const int64_t lt = tile - V.tile_off;
+    const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
+    const bool inside = px < V.W && py < V.H;
+    const uint2 rg = ranges[tile];
+    const int RW = vt.rec_words, FW = vt.feat_word;
+    const float amax = vt.alpha_max, tmin = vt.t_min;
+
+    float T = 1.f, A = 0.f, Dp = 0.f;
+    float F[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) F[c] = 0.f;
+    uint32_t last = 0, stop = 0;
+    bool done = !inside;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
+    if (tid == 0) s_maxstop = 0;
+
+    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBatch) {
+        if (__syncthreads_count(!done) == 0) break;
+        const uint32_t q = b0 + tid;
+        if (q < rg.y) {
+            const uint32_t gi = pts[q];
+            const uint32_t* rp = rec + (size_t)gi * RW;
+            const uint4 g = *reinterpret_cast<const uint4*>(rp);
+            float f[C];
+            load_features<C, BF16>(rp + FW, f);
+            const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
+            s_a[tid] = bg.a;
+            s_b[tid] = bg.b;
+            s_o[tid] = __uint_as_float(g.w);
+            s_z[tid] = __uint_as_float(g.z);
+            s_i0[tid] = bg.i0;
+            s_j0[tid] = bg.j0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) s_f[c][tid] = f[c];
+            const int X0 = bg.i0 - tx * kTile, Y0 = bg.j0 - ty * kTile;
+            const uint32_t bit = 1u << lane;
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                const int Y = Y0 + dy;
+                if ((unsigned)Y >= (unsigned)kTile) continue;
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int X = X0 + dx;
+                    if ((unsigned)X < (unsigned)kTile) atomicOr(&s_mask[Y * kTile + X][warp], bit);
+                }
+            }
+        }
+        __syncthreads();
+        if (!done) {
+            const uint32_t rel0 = b0 - rg.x;
+#pragma unroll 1
+            for (int w = 0; w < 8 && !done; ++w) {
+                uint32_t m = s_mask[tid][w];
+                while (m) {
+                    const int r = w * 32 + __ffs(m) - 1;
+                    m &= m - 1;
+                    const float wgt = bilin_weight(px, py, s_i0[r], s_j0[r], s_a[r], s_b[r]);
+                    const float alpha = fminf(__fmul_rn(s_o[r], wgt), amax);
+                    const float nT = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                    if (nT < tmin) {
+                        done = true;
+                        stop = rel0 + r + 1;
+                        break;
+                    }
+                    const float ta = T * alpha;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) F[c] = fmaf(ta, s_f[c][r], F[c]);
+                    Dp = fmaf(ta, s_z[r], Dp);
+                    A += ta;
+                    T = nT;
+                    last = rel0 + r + 1;
+                }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
+    }
+
+    if (inside) {
+        const int64_t pix = (int64_t)py * V.W + px;
+        float* of = V.out_feat + pix * C;
+#pragma unroll
+        for (int c = 0; c < C; ++c) of[c] = F[c];
+        if (V.out_alpha) V.out_alpha[pix] = A;
+        if (V.out_depth) V.out_depth[pix] = Dp;
+        t_final[V.pix_off + pix] = T;
+        last_out[V.pix_off + pix] = last;
+    }
+    const int open = __syncthreads_or(inside && stop == 0);
+    if (stop) atomicMax(&s_maxstop, stop);
+    __syncthreads();
+    if (tid == 0)
+        atomicAdd(&hdr->needed, (unsigned long long)(open ? (rg.y - rg.x) : s_maxstop));
+}
+
+constexpr int kGroups = kBatch / 32;
+
+template <int C, bool BF16>
+__global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
+    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pts,
+    const uint32_t* __restrict__ rec, float* __restrict__ t_final, uint32_t* __restrict__ last_out,
+    WsHeader* __restrict__ hdr) {
+    __shared__ float s_um[kBatch], s_vm[kBatch], s_o[kBatch], s_z[kBatch];
+    __shared__ float s_ca[kBatch], s_cb[kBatch], s_cc[kBatch];
+    __shared__ int4 s_box[kBatch];
+    __shared__ float s_f[C][kBatch];
+    __shared__ uint32_t s_maxstop;
+
+    const int64_t tile = blockIdx.x;
+    const ViewDev& V = vt.v[view_of_tile(vt, tile)];
+    const int64_t lt = tile - V.tile_off;
+    const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // warp -> 8x4 sub-tile
+    const int sx0 = tx * kTile + (warp & 1) * 8, sy0 = ty * kTile + (warp >> 1) * 4;
+    const int px = sx0 + (lane & 7), py = sy0 + (lane >> 3);
+    const bool inside = px < V.W && py < V.H;
+    const uint2 rg = ranges[tile];
+    const int RW = vt.rec_words, FW = vt.feat_word;
+    const float amax = vt.alpha_max, tmin = vt.t_min;
+    const float fpx = (float)px, fpy = (float)py;
+
+    float T = 1.f, A = 0.f, Dp = 0.f;
+    float F[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) F[c] = 0.f;
+    uint32_t last = 0, stop = 0;
+    bool done = !inside;
+    if (tid == 0) s_maxstop = 0;
+
+    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBatch) {
+        if (__syncthreads_count(!done) == 0) break;
+        const uint32_t q = b0 + tid;
+        if (q < rg.y) {
+            const uint32_t gi = pts[q];
+            const uint32_t* rp = rec + (size_t)gi * RW;
+            const uint4 g = *reinterpret_cast<const uint4*>(rp);
+            const uint4 h = *reinterpret_cast<const uint4*>(rp + 4);
+            float f[C];
+            load_features<C, BF16>(rp + FW, f);
+            const float um = __fsub_rn(__uint_as_float(g.x), 0.5f);
+            const float vm = __fsub_rn(__uint_as_float(g.y), 0.5f);
+            const GaussBox bx = gauss_box(um, vm, __uint_as_float(h.w));
+            s_um[tid] = um;
+            s_vm[tid] = vm;
+            s_z[tid] = __uint_as_float(g.z);
+            s_o[tid] = __uint_as_float(g.w);
+            s_ca[tid] = __uint_as_float(h.x);
+            s_cb[tid] = __uint_as_float(h.y);
+            s_cc[tid] = __uint_as_float(h.z);
+            s_box[tid] = make_int4(bx.x0, bx.x1, bx.y0, bx.y1);
+#pragma unroll
+            for (int c = 0; c < C; ++c) s_f[c][tid] = f[c];
+        }
+        __syncthreads();
+        const int nrec = (int)min((uint32_t)kBatch, rg.y - b0);
+        const uint32_t rel0 = b0 - rg.x;
+        if (!__all_sync(0xffffffffu, done)) {
+#pragma unroll 1
+            for (int grp = 0; grp < kGroups; ++grp) {
+                const int r0 = grp * 32;
+                if (r0 >= nrec) break;
+                bool hit = false;
+                if (r0 + lane < nrec) {
+                    const int4 bb = s_box[r0 + lane];
+                    hit = bb.x <= sx0 + 7 && bb.y >= sx0 && bb.z <= sy0 + 3 && bb.w >= sy0;
+                }
+                uint32_t m = __ballot_sync(0xffffffffu, hit);
+                while (m) {
+                    const int r = r0 + __ffs(m) - 1;
+                    m &= m - 1;
+                    if (!done) {
+                        const int4 bb = s_box[r];
+                        if (px >= bb.x && px <= bb.y && py >= bb.z && py <= bb.w) {
+                            const float dx = __fsub_rn(fpx, s_um[r]), dy = __fsub_rn(fpy, s_vm[r]);
+                            const float mm = gauss_m(dx, dy, s_ca[r], s_cb[r], s_cc[r]);
+                            if (mm <= 9.f) {
+                                const float alpha = fminf(__fmul_rn(s_o[r], gauss_value(mm)), amax);
+                                const float nT = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                                if (nT < tmin) {
+                                    done = true;
+                                    stop = rel0 + r + 1;
+                                } else {
+                                    const float ta = T * alpha;
+#pragma unroll
+                                    for (int c = 0; c < C; ++c) F[c] = fmaf(ta, s_f[c][r], F[c]);
+                                    Dp = fmaf(ta, s_z[r], Dp);
+                                    A += ta;
+                                    T = nT;
+                                    last = rel0 + r + 1;
+                                }
+                            }
+                        }
+                    }
+                }
+                if (__all_sync(0xffffffffu, done)) break;
+            }
+        }
+    }
+
+    if (inside) {
+        const int64_t pix = (int64_t)py * V.W + px;
+        float* of = V.out_feat + pix * C;
+#pragma unroll
+        for (int c = 0; c < C; ++c) of[c] = F[c];
+        if (V.out_alpha) V.out_alpha[pix] = A;
+        if (V.out_depth) V.out_depth[pix] = Dp;
+        t_final[V.pix_off + pix] = T;
+        last_out[V.pix_off + pix] = last;
+    }
+    const int open = __syncthreads_or(inside && stop == 0);
+    if (stop) atomicMax(&s_maxstop, stop);
+    __syncthreads();
+    if (tid == 0)
+        atomicAdd(&hdr->needed, (unsigned long long)(open ? (rg.y - rg.x) : s_maxstop));
+}
+
+template <int C, bool BF16>
+cudaError_t launch_fwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    const unsigned grid = (unsigned)vt.tiles_total;
+    if (vt.mode == 0)
+        k_blend_fwd_bilinear<C, BF16><<<grid, kBlendThreads, 0, s>>>(vt, b.ranges, pts, b.rec,
+                                                                     b.t_final, b.last, b.hdr);
+    else
+        k_blend_fwd_gauss<C, BF16><<<grid, kBlendThreads, 0, s>>>(vt, b.ranges, pts, b.rec,
+                                                                  b.t_final, b.last, b.hdr);
+    return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t launch_fwd_c(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    return vt.bf16 ? launch_fwd_t<C, true>(vt, b, pts, s) : launch_fwd_t<C, false>(vt, b, pts, s);
+}
+
+}  // namespace
+
+bool channels_supported(int C) {
+    return C == 1 || C == 2 || C == 3 || C == 4 || C == 8 || C == 16;
+}
+
+cudaError_t launch_blend_fwd(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    if (vt.tiles_total == 0) return cudaSuccess;
+    switch (vt.C) {
+        case 1: return launch_fwd_c<1>(vt, b, pts, s);
+        case 2: return launch_fwd_c<2>(vt, b, pts, s);
+        case 3: return launch_fwd_c<3>(vt, b, pts, s);
+        case 4: return launch_fwd_c<4>(vt, b, pts, s);
+        case 8: return launch_fwd_c<8>(vt, b, pts, s);
+        case 16: return launch_fwd_c<16>(vt, b, pts, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rast

@@ -1,0 +1,229 @@
+// K2 + K3 + K5: copies of each point per touched tile, and per-tile ranges.
+//
+// Second half of the split sort of Sec. 3.2 ("Tiled Rendering"): after the
+// points are sorted by depth, each point (in depth order) writes one copy per
+// tile its footprint touches, keyed by the global tile id. Writing the copies
+// in depth order and sorting them stably by tile id afterwards yields the
+// (tile, depth, point index) order. The copy offsets come from an exclusive
+// scan of the per-point tile counts in depth order; the total D stays on the
+// device and is clamped to the workspace capacity (overflow sets the
+// capacity bit of the error word; no write ever leaves the buffers).
+#include "rast_internal.cuh"
+
+namespace rast {
+namespace {
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp, uint32_t& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    const uint32_t inc = warp_incl_scan(x);
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NW ? s_warp[lane] : 0u;
+        const uint32_t wi = warp_incl_scan(w);
+        if (lane < NW) s_warp[lane] = wi - w;
+        if (lane == NW - 1) s_warp[31] = wi;
+    }
+    __syncthreads();
+    const uint32_t res = s_warp[warp] + inc - x;
+    total = s_warp[31];
+    __syncthreads();
+    return res;
+}
+
+constexpr int kT = 256;
+constexpr int kPer = kScanItems / kT;  // 4 items per thread, striped
+
+// rectS[s] = rect[sorted_pts[s]]; block sums of the tile counts.
+__global__ void __launch_bounds__(kT) k_dup_count(const uint32_t* __restrict__ sorted_pts,
+                                                  const uint2* __restrict__ rect,
+                                                  uint2* __restrict__ rectS, int64_t n,
+                                                  uint32_t* __restrict__ blk) {
+    __shared__ uint32_t s_warp[32];
+    const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int64_t s = b0 + j * kT + threadIdx.x;
+        if (s < n) {
+            const uint2 r = rect[sorted_pts[s]];
+            rectS[s] = r;
+            c += rect_count(r);
+        }
+    }
+    uint32_t tot;
+    block_excl_scan<kT>(c, s_warp, tot);
+    if (threadIdx.x == 0) blk[blockIdx.x] = tot;
+}
+
+// Block sums of a per-point count array (point order).
+__global__ void __launch_bounds__(kT) k_count_blocks(const uint32_t* __restrict__ cnt, int64_t n,
+                                                     uint32_t* __restrict__ blk) {
+    __shared__ uint32_t s_warp[32];
+    const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int64_t s = b0 + j * kT + threadIdx.x;
+        if (s < n) c += cnt[s];
+    }
+    uint32_t tot;
+    block_excl_scan<kT>(c, s_warp, tot);
+    if (threadIdx.x == 0) blk[blockIdx.x] = tot;
+}
+
+// Exclusive scan of nb block sums in place (one block). If hdr is given the
+// total is the copy count D, summed in 64 bits: if it exceeds the capacity the
+// capacity bit is raised and D is published as 0, so every later stage sees an
+// empty copy list instead of a truncated one.
+__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ blk, int64_t nb,
+                                                      WsHeader* hdr, int64_t cap) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ unsigned long long s_total;
+    if (threadIdx.x == 0) s_total = 0ull;
+    __syncthreads();
+    const int64_t per = (nb + 1023) / 1024;
+    const int64_t lo = threadIdx.x * per;
+    const int64_t hi = lo + per < nb ? lo + per : nb;
+    unsigned long long s = 0;
+    for (int64_t t = lo; t < hi; ++t) s += blk[t];
+    atomicAdd(&s_total, s);
+    uint32_t tot;
+    uint32_t run = block_excl_scan<1024>((uint32_t)s, s_warp, tot);  // exact whenever total <= cap
+    for (int64_t t = lo; t < hi; ++t) {
+        const uint32_t c = blk[t];
+        blk[t] = run;
+        run += c;
+    }
+    if (hdr && threadIdx.x == 0) {
+        const unsigned long long total = s_total;
+        const bool over = total > (unsigned long long)cap;
+        hdr->n_copies_raw = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+        hdr->n_copies = over ? 0u : (uint32_t)total;
+        if (over) atomicOr(&hdr->error, kErrCapacity);
+    }
+}
+
+// Writes the copies: key = global tile id, value = global point index.
+__global__ void __launch_bounds__(kT) k_dup_write(const ViewTable vt, const uint32_t* __restrict__ sorted_pts,
+                                                  const uint2* __restrict__ rectS, int64_t n,
+                                                  const uint32_t* __restrict__ blk,
+                                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                  int64_t cap) {
+    __shared__ uint32_t s_warp[32];
+    const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
+    uint32_t off = blk[blockIdx.x];
+#pragma unroll 1
+    for (int j = 0; j < kPer; ++j) {
+        const int64_t s = b0 + j * kT + threadIdx.x;
+        uint2 r = make_uint2(1u, 0u);
+        if (s < n) r = rectS[s];
+        const uint32_t c = rect_count(r);
+        uint32_t tot;
+        uint32_t o = off + block_excl_scan<kT>(c, s_warp, tot);
+        off += tot;
+        if (c) {
+            const uint32_t gi = sorted_pts[s];
+            const ViewDev& V = vt.v[view_of_point(vt, gi)];
+            const int tx0 = r.x & 0xffff, ty0 = r.x >> 16, tx1 = r.y & 0xffff, ty1 = r.y >> 16;
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) {
+                    if ((int64_t)o < cap) {
+                        keys[o] = (uint32_t)(V.tile_off + (int64_t)ty * V.tiles_x + tx);
+                        vals[o] = gi;
+                    }
+                    ++o;
+                }
+        }
+    }
+}
+
+// base[i] = exclusive prefix of cnt in point order.
+__global__ void __launch_bounds__(kT) k_scan_apply(const uint32_t* __restrict__ cnt, int64_t n,
+                                                   const uint32_t* __restrict__ blk,
+                                                   uint32_t* __restrict__ base) {
+    __shared__ uint32_t s_warp[32];
+    const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
+    uint32_t off = blk[blockIdx.x];
+#pragma unroll 1
+    for (int j = 0; j < kPer; ++j) {
+        const int64_t s = b0 + j * kT + threadIdx.x;
+        const uint32_t c = s < n ? cnt[s] : 0u;
+        uint32_t tot;
+        const uint32_t o = off + block_excl_scan<kT>(c, s_warp, tot);
+        off += tot;
+        if (s < n) base[s] = o;
+    }
+}
+
+// Tile ranges [start, end) from the tile-sorted keys (ranges pre-zeroed).
+__global__ void __launch_bounds__(kT) k_ranges(const uint32_t* __restrict__ keys,
+                                               const WsHeader* __restrict__ hdr,
+                                               uint2* __restrict__ ranges) {
+    const int64_t D = hdr->n_copies;
+    for (int64_t p = (int64_t)blockIdx.x * kT + threadIdx.x; p < D; p += (int64_t)gridDim.x * kT) {
+        const uint32_t t = keys[p];
+        if (p == 0 || keys[p - 1] != t) ranges[t].x = (uint32_t)p;
+        if (p + 1 == D || keys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+    }
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+}  // namespace
+
+cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
+                             cudaStream_t s) {
+    const int64_t n = vt.n_total;
+    const int64_t nb = (n + kScanItems - 1) / kScanItems;
+    if (nb == 0) return cudaSuccess;  // the header was zeroed at the start of the pass
+    k_dup_count<<<(unsigned)nb, kT, 0, s>>>(sorted_pts, b.rect, b.rectS, n, b.blk);
+    k_scan_blocks<<<1, 1024, 0, s>>>(b.blk, nb, b.hdr, b.copy_cap);
+    k_dup_write<<<(unsigned)nb, kT, 0, s>>>(vt, sorted_pts, b.rectS, n, b.blk, b.keyC[0], b.valC[0],
+                                           b.copy_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_tiles,
+                          cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.ranges, 0, sizeof(uint2) * vt.tiles_total, s);
+    if (e != cudaSuccess || b.copy_cap == 0) return e;
+    int64_t g = (b.copy_cap + kT - 1) / kT;
+    const int64_t gmax = (int64_t)sm_count() * 8;
+    if (g > gmax) g = gmax;
+    k_ranges<<<(unsigned)g, kT, 0, s>>>(sorted_tiles, b.hdr, b.ranges);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_point_scan(const ViewTable& vt, const Bufs& b, cudaStream_t s) {
+    const int64_t n = vt.n_total;
+    const int64_t nb = (n + kScanItems - 1) / kScanItems;
+    if (nb == 0) return cudaSuccess;
+    k_count_blocks<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk);
+    k_scan_blocks<<<1, 1024, 0, s>>>(b.blk, nb, nullptr, 0);
+    k_scan_apply<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk, b.base);
+    return cudaGetLastError();
+}
+
+}  // namespace rast

@@ -1,0 +1,171 @@
+// Internal declarations of the GB300 tiled point rasterizer (sm_103a).
+// Shared by the kernel translation units and the C-ABI layer in api.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "inpc_rast.h"
+
+namespace rast {
+
+constexpr int kMaxViews = 16;
+constexpr int kTile = 16;            // tile edge (pixels)
+constexpr int kTilePix = kTile * kTile;
+constexpr int kBlendThreads = 256;   // one thread per pixel of a 16x16 tile
+constexpr int kBatch = 256;          // records staged per blend batch
+
+// Status bits in the workspace header's error word.
+constexpr uint32_t kErrCapacity = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+
+// One view as the kernels see it (passed by value inside ViewTable).
+struct ViewDev {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float near_z, far_z;
+    int32_t W, H, tiles_x, tiles_y;
+    uint32_t key_base;   // FP32 bits of near_z: depth key = bits(z) - key_base
+    uint32_t key_cull;   // key of culled points: bits(far) - bits(near) (> every visible key)
+    int64_t pt_off;      // first global point index
+    int64_t n;
+    int64_t tile_off;    // first global tile id
+    int64_t pix_off;     // first global pixel
+    const float* xyz;
+    const float* opacity;
+    const void* feat;
+    const float* scale;
+    float* out_feat;
+    float* out_alpha;
+    float* out_depth;
+    const float* g_feat;
+    const float* g_alpha;
+    const float* g_depth;
+    float* d_feat;
+    float* d_opacity;
+    float* d_xyz;
+    float* d_scale;
+};
+
+struct ViewTable {
+    int32_t n_views;
+    int32_t C;
+    int32_t bf16;        // features stored as bf16
+    int32_t mode;        // 0 bilinear, 1 Gaussian
+    int32_t gauss_cov;   // 0 EWA, 1 isotropic screen
+    int32_t rec_words;   // record stride in 32-bit words (multiple of 4)
+    int32_t feat_word;   // first feature word in a record
+    float t_min, alpha_max, dilation;
+    int64_t n_total, tiles_total, pix_total;
+    ViewDev v[kMaxViews];
+};
+
+// Device header at the start of the workspace.
+struct WsHeader {
+    uint32_t error;
+    uint32_t n_copies;        // D after the dup scan (clamped to capacity)
+    uint32_t n_copies_raw;    // D before clamping
+    uint32_t n_views;
+    unsigned long long needed;  // records the blend had to read
+    long long n_points, copy_cap, n_tiles, n_pixels;
+    long long pad[3];
+};
+
+// ---- small device helpers --------------------------------------------------
+
+__device__ __forceinline__ int view_of_point(const ViewTable& vt, int64_t gi) {
+    int v = 0;
+#pragma unroll 1
+    for (int k = 1; k < vt.n_views; ++k)
+        if (gi >= vt.v[k].pt_off) v = k;
+    return v;
+}
+
+__device__ __forceinline__ int view_of_tile(const ViewTable& vt, int64_t t) {
+    int v = 0;
+#pragma unroll 1
+    for (int k = 1; k < vt.n_views; ++k)
+        if (t >= vt.v[k].tile_off) v = k;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// Packed tile rect of a point: (tx0 | ty0 << 16, tx1 | ty1 << 16), inclusive;
+// an empty rect is (1, 0) (tx0 > tx1).
+__device__ __forceinline__ uint32_t rect_count(uint2 r) {
+    const int tx0 = r.x & 0xffff, ty0 = r.x >> 16, tx1 = r.y & 0xffff, ty1 = r.y >> 16;
+    if (tx1 < tx0 || ty1 < ty0) return 0;
+    return (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+}
+
+// ---- launchers (each defined in its own translation unit) ------------------
+
+struct Bufs {
+    // per point
+    uint32_t* rec;        // records, rec_words per point
+    uint2* rect;          // tile rect per point
+    uint32_t* cnt;        // copies per point (point order)
+    uint32_t* keyA[2];    // depth sort ping-pong
+    uint32_t* valA[2];
+    uint2* rectS;         // rects in depth order
+    uint32_t* blk;        // block sums for scans
+    uint32_t* base;       // point-order exclusive scan of cnt (backward)
+    // per copy
+    uint32_t* keyC[2];
+    uint32_t* valC[2];
+    float* partial;       // backward per-copy partial gradients
+    // radix sort scratch
+    uint32_t* hist;       // [bins][hist_tiles]
+    uint32_t* bin_total;  // [passes][512]
+    // per tile / pixel
+    uint2* ranges;
+    uint2* cutoff;        // backward: (depth bits, point) of the last record processed per tile
+    float* t_final;
+    uint32_t* last;
+    WsHeader* hdr;
+    int64_t copy_cap;
+    int64_t hist_tiles;
+    int64_t blk_cap;
+};
+
+// Sort plan for one radix sort: digit passes over [0, bits).
+struct SortPlan {
+    int passes;
+    int digit_bits[8];
+    int shift[8];
+};
+SortPlan make_sort_plan(int bits);
+int64_t sort_hist_tiles(int64_t cap);
+
+cudaError_t launch_project(const ViewTable& vt, const Bufs& b, cudaStream_t s);
+// Stable LSD radix sort of (key, val) pairs in keys[0]/vals[0] using keys[1]/vals[1]
+// as scratch; count from d_n (device) if non-null else n. Returns the index (0/1)
+// of the buffer that holds the result.
+cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n,
+                       int64_t cap, const SortPlan& plan, uint32_t* hist, int64_t hist_tiles,
+                       uint32_t* bin_total, cudaStream_t s, int* result_buf);
+cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
+                             cudaStream_t s);
+cudaError_t launch_ranges(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_tiles,
+                          cudaStream_t s);
+cudaError_t launch_blend_fwd(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
+                             cudaStream_t s);
+cudaError_t launch_point_scan(const ViewTable& vt, const Bufs& b, cudaStream_t s);
+cudaError_t launch_blend_bwd(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
+                             cudaStream_t s);
+cudaError_t launch_reduce_grads(const ViewTable& vt, const Bufs& b, cudaStream_t s);
+
+bool channels_supported(int C);
+
+constexpr int kScanItems = 1024;   // items per block in the dup / point scans
+
+}  // namespace rast
