@@ -1,0 +1,472 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 tiled point rasterizer.
+
+Metric: splatted points/s for one forward + backward pass (the whole hot
+path: projection, split radix sort, duplication, tile ranges, blend, replay
+backward, per-point reduction) on the training-shape workload: 4,194,304
+clustered points (64 anisotropic Gaussian clusters + 10% uniform background),
+opacity ~ Beta(2, 2), 4 FP32 features, one 1280x832 view, bilinear splats,
+upstream gradients ~ N(0, 1). Inputs are seeded and synthetic.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With torchrun (N > 1) every rank renders its own independent frame (weak
+scaling, no collective on the data path); the time is the max over ranks.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "splatted points/s (fwd+bwd) at 1280x832"
+UNIT = "points/s"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2, help="workload id (2: 4M points, 1280x832)")
+    ap.add_argument("--scale-points", type=float, default=1.0, help="shrink the point count (tests)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- algorithmic bytes
+
+def kernel_bytes(name, w):
+    """Algorithmic DRAM bytes of ONE launch of kernel `name` on workload counts w."""
+    N, D, Dn, Db, HW, C, P = w["N"], w["D"], w["needed"], w["needed_bwd"], w["HW"], w["C"], w["P"]
+    rec, fb, npart = w["rec_bytes"], w["feat_bytes"], w["partial_floats"]
+    if name == "project":
+        return N * (12 + 4 + C * fb) + N * (rec + 4 + 4 + 8 + 4)
+    if name.endswith(".hist"):
+        return 4 * (N if name.startswith("depth") else D)
+    if name.endswith(".scatter"):
+        return 16 * (N if name.startswith("depth") else D)
+    if name == "dup.count":
+        return N * (4 + 8 + 8)
+    if name == "dup.write":
+        return N * (8 + 4) + D * 8
+    if name == "ranges":
+        return D * 4 + P * 8
+    if name == "blend_fwd":
+        return Dn * (rec + 4) + P * 8 + HW * (4 * C + 16)
+    if name == "point_scan.count":
+        return N * 4
+    if name == "point_scan.apply":
+        return N * 8
+    if name == "blend_bwd":
+        return Db * (rec + 4 + 12 + 4 * npart) + P * 16 + HW * (4 * C + 16)
+    if name == "reduce_grads":
+        return N * (8 + 4 + 4) + Db * 4 * npart + N * (4 * C + 4)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, ws_, rank, local):
+    import torch
+
+    from paper_2508_19140_gb300 import build as build_mod
+    from paper_2508_19140_gb300 import rast, scenes
+
+    build_mod.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if ws_ > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    scene = scenes.make_scene(args.config, seed=1000 + args.config + 7919 * rank,
+                              scale_points=args.scale_points)
+    bf16 = scene.feat_dtype == "bf16"
+    gauss = scene.mode == "gaussian"
+    opts = rast.make_opts(mode=scene.mode)
+    tens, cviews = [], []
+    for v in scene.views:
+        t = {}
+        t["xyz"] = torch.from_numpy(v.xyz).to(dev)
+        t["op"] = torch.from_numpy(v.opacity).to(dev)
+        t["feat"] = torch.from_numpy(v.feat).to(dev, torch.bfloat16 if bf16 else torch.float32)
+        t["scale"] = torch.from_numpy(v.scale).to(dev) if (gauss and v.scale is not None) else None
+        H, W, C = v.camera.height, v.camera.width, v.feat.shape[1]
+        n = v.xyz.shape[0]
+        t["F"] = torch.empty((H, W, C), device=dev)
+        t["A"] = torch.empty((H, W), device=dev)
+        t["D"] = torch.empty((H, W), device=dev)
+        t["gF"] = torch.from_numpy(v.g_feat).to(dev)
+        t["gA"] = torch.from_numpy(v.g_alpha).to(dev)
+        t["gD"] = torch.from_numpy(v.g_depth).to(dev)
+        t["d_feat"] = torch.empty((n, C), device=dev)
+        t["d_op"] = torch.empty((n,), device=dev)
+        t["d_xyz"] = torch.empty((n, 3), device=dev) if gauss else None
+        t["d_scale"] = torch.empty((n,), device=dev) if t["scale"] is not None else None
+        cv = rast.View()
+        cv.pts = rast.make_points(t["xyz"], t["op"], t["feat"], t["scale"])
+        cv.cam = rast.make_camera(v.camera)
+        cv.out = rast.make_images(t["F"], t["A"], t["D"])
+        cv.grad = rast.make_grads(t["gF"], t["gA"], t["gD"], t["d_feat"], t["d_op"], t["d_xyz"], t["d_scale"])
+        tens.append(t)
+        cviews.append(cv)
+    ws_bytes = rast.rasterize_workspace_size(cviews, opts)
+    wsp = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    n_points = sum(v.xyz.shape[0] for v in scene.views)
+    do_bwd = scene.backward
+
+    def step():
+        rast.rasterize_batch(cviews, rast.PASS_FWD | (rast.PASS_BWD if do_bwd else 0), opts, wsp, stream)
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    st, stats = rast.rasterize_get_status(wsp, stream)
+    if st != rast.RAST_OK:
+        raise RuntimeError(f"rasterizer status {st}: {stats}")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    rast.rasterize_profile_enable(True)
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    prof = rast.rasterize_profile_read()
+    rast.rasterize_profile_enable(False)
+    st, stats = rast.rasterize_get_status(wsp, stream)  # counters of the last fwd+bwd step
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+
+    # Forward-only timing (reported beside the headline).
+    fwd_ms = None
+    if do_bwd:
+        evf = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rast.rasterize_batch(cviews, rast.PASS_FWD, opts, wsp, stream)
+            e1.record(stream)
+            evf.append((e0, e1))
+        torch.cuda.synchronize()
+        fwd_ms = sum(a.elapsed_time(b) for a, b in evf) / len(evf)
+
+    ms_step = total_ms / max(args.steps, 1)
+    value = n_points * ws_ / (ms_step / 1e3)
+
+    # ---- roofline of the dominant kernel (per-launch averages from the live events)
+    v0 = scene.views[0]
+    C = v0.feat.shape[1]
+    lay = rast.rasterize_workspace_layout(cviews, opts)
+    rec_bytes = lay["records"][1] // max(n_points, 1)
+    w = dict(N=n_points, D=int(stats["n_copies"]), needed=int(stats["needed_records"]),
+             needed_bwd=int(stats["needed_records_bwd"]),
+             HW=sum(v.camera.width * v.camera.height for v in scene.views), C=C,
+             P=int(stats["n_tiles"]), rec_bytes=rec_bytes, feat_bytes=2 if bf16 else 4,
+             partial_floats=C + (7 if gauss else 1))
+    peak, peak_src = measured_peak_hbm()
+    kernels = {}
+    for name, (launches, tot) in prof.items():
+        avg = tot / max(launches, 1)
+        b = kernel_bytes(name, w)
+        kernels[name] = dict(launches=launches, ms_per_launch=round(avg, 5),
+                             share=round(tot / max(sum(x[1] for x in prof.values()), 1e-9), 4),
+                             bytes=int(b), gbs=round(b / (avg * 1e6), 1) if avg > 0 else None)
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    roofline = None
+    if dom:
+        k = kernels[dom]
+        ach = k["gbs"] or 0.0
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": round(ach / peak, 4), "traffic": None,
+                    "peak_source": f"{peak_src} (hbm_gbs)"}
+    blend = kernels.get("blend_fwd")
+    gpu_launches = int(sum(x[0] for x in prof.values()))
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, scene, tens, cviews, opts, wsp, stream, dev, n_points, ws_, dist)
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws_,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16-features/f32" if bf16 else "f32", "data": "synthetic",
+        "config": {"workload": scene.name, "config_id": scene.config_id, "n_points_per_gpu": n_points,
+                   "views": len(scene.views), "width": v0.camera.width, "height": v0.camera.height,
+                   "channels": C, "mode": scene.mode, "pass": "fwd+bwd" if do_bwd else "fwd",
+                   "l2": "flushed between timed steps (256 MiB write, untimed)",
+                   "parallelism": f"independent frame per GPU x{ws_}"},
+        "fwd_points_per_s": round(n_points * ws_ / (fwd_ms / 1e3), 1) if fwd_ms else None,
+        "ms_fwd": round(fwd_ms, 4) if fwd_ms else None,
+        "copies": w["D"], "needed_records": w["needed"],
+        "roofline": roofline,
+        "blend_fwd_roofline": ({"achieved": blend["gbs"], "peak": peak, "unit": "GB/s",
+                                "frac": round((blend["gbs"] or 0) / peak, 4)} if blend else None),
+        "kernels": kernels, "gpu_launches": gpu_launches,
+        "clocks": clocks, "e2e": e2e,
+    }
+    return out, dist
+
+
+def run_e2e(args, scene, tens, cviews, opts, wsp, stream, dev, n_points, ws_, dist):
+    """Same metric through the C ABI with pinned HOST buffers: every step copies
+    the inputs host->device, runs fwd+bwd and copies the outputs back."""
+    import torch
+
+    from paper_2508_19140_gb300 import rast
+
+    host_in, host_out = [], []
+    h2d = d2h = 0
+    for t in tens:
+        hi = {k: t[k].detach().cpu().pin_memory() for k in ("xyz", "op", "feat", "gF", "gA", "gD")
+              if t.get(k) is not None}
+        if t.get("scale") is not None:
+            hi["scale"] = t["scale"].cpu().pin_memory()
+        ho = {k: torch.empty(t[k].shape, dtype=t[k].dtype, pin_memory=True)
+              for k in ("F", "A", "D", "d_feat", "d_op") if t.get(k) is not None}
+        h2d += sum(x.numel() * x.element_size() for x in hi.values())
+        d2h += sum(x.numel() * x.element_size() for x in ho.values())
+        host_in.append(hi)
+        host_out.append(ho)
+
+    def step():
+        for t, hi in zip(tens, host_in):
+            for k, x in hi.items():
+                t[k].copy_(x, non_blocking=True)
+        rast.rasterize_batch(cviews, rast.PASS_FWD | (rast.PASS_BWD if scene.backward else 0), opts, wsp, stream)
+        for t, ho in zip(tens, host_out):
+            for k, x in ho.items():
+                x.copy_(t[k], non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    K = max(3, args.steps // 2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    if dist:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    return {"value": round(n_points * ws_ / (ms / 1e3), 1), "unit": UNIT, "ms_per_step": round(ms, 4),
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "api": "rasterize_batch (C ABI) with pinned host buffers"}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(scene, budget_s, threads=0, pin32=True):
+    """Time the CPU oracle (as it stands) on a band of pixel rows of the same
+    frame: forward for the band's pixels, backward for the points that land in
+    it. The band height is chosen so the run fits the budget. Returns
+    (points/s, points in the sample, seconds, description)."""
+    import oracle
+
+    v = scene.views[0]
+    kw = dict(mode=scene.mode, tile=16, pin32=pin32, n_threads=threads)
+    W, H = v.camera.width, v.camera.height
+    p = oracle.project(v.xyz, v.camera, scale=v.scale if scene.mode == "gaussian" else None, **kw)
+    vis = p["vis"] == 1
+    feat = v.feat.astype(np.float64)
+
+    def run(rows):
+        y0 = (H - rows) // 2
+        pix = (np.arange(y0, y0 + rows)[:, None] * W + np.arange(W)[None, :]).reshape(-1)
+        pm = vis & (p["box"][:, 2] >= y0) & (p["box"][:, 3] < y0 + rows)
+        t = time.perf_counter()
+        oracle.render(v.xyz, v.opacity, feat, v.camera, pix=pix, scale=v.scale, **kw)
+        if scene.backward:
+            oracle.backward(v.xyz, v.opacity, feat, v.camera, v.g_feat, v.g_alpha, v.g_depth,
+                            scale=v.scale, pmask=pm.astype(np.uint8), **kw)
+        return time.perf_counter() - t, int(pm.sum()), rows
+
+    dt, npts, rows = run(max(H // 32, 1))
+    per_pt = dt / max(npts, 1)
+    rows = H
+    if per_pt * vis.sum() > budget_s:
+        rows = max(1, min(H, int(H * budget_s / max(per_pt * vis.sum(), 1e-9))))
+    dt, npts, rows = run(rows)
+    desc = (f"oracle fwd{'+bwd' if scene.backward else ''} on a band of {rows}/{H} pixel rows of the "
+            f"{W}x{H} frame ({npts} of {len(v.xyz)} points land in it), FP64 values / FP32 decisions")
+    return npts / dt, npts, dt, desc
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return None
+    import oracle
+
+    from paper_2508_19140_gb300 import scenes
+
+    oracle.build()
+    scene = scenes.make_scene(args.config, scale_points=args.scale_points)
+    steps = max(args.steps, 1)
+    budget = max(1.0, 150.0 / (steps + min(args.warmup, 1)))
+    vals = []
+    desc = ""
+    for k in range(min(args.warmup, 1) + steps):
+        val, npts, dt, desc = oracle_sample(scene, budget)
+        if k >= min(args.warmup, 1):
+            vals.append((npts, dt))
+    tot_pts = sum(x[0] for x in vals)
+    tot_t = sum(x[1] for x in vals)
+    value = tot_pts / tot_t
+    cores = oracle.num_threads()
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot_t / steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": scene.name, "config_id": scene.config_id},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws_, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out, dist = run_ours(args, ws_, rank, local)
+    if rank == 0 and not args.no_cpu_baseline and ws_ == 1:
+        from paper_2508_19140_gb300 import scenes
+        import oracle
+        oracle.build()
+        scene = scenes.make_scene(args.config, scale_points=args.scale_points)
+        val, npts, dt, desc = oracle_sample(scene, args.cpu_budget_s)
+        out["cpu_baseline"] = {"value": round(val, 1), "unit": UNIT, "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": desc, "seconds": round(dt, 2)}
+    elif rank == 0:
+        out["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

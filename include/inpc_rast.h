@@ -123,6 +123,7 @@ typedef struct {
     int64_t needed_records;  /* records the blend had to read (after early termination) */
     int64_t n_tiles;
     int64_t n_pixels;
+    int64_t needed_records_bwd; /* records the backward replay read (last backward) */
 } rast_stats_t;
 
 /* One row of the per-stage timing profile. */

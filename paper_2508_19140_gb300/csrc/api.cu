@@ -36,14 +36,14 @@ int bit_length(uint64_t x) {
 }
 
 enum Slot {
-    S_HDR, S_REC, S_RECT, S_CNT, S_KEYA0, S_KEYA1, S_VALA0, S_VALA1, S_RECTS, S_BASE, S_BLK,
-    S_KEYC0, S_KEYC1, S_VALC0, S_VALC1, S_PARTIAL, S_HIST, S_BINTOT, S_RANGES, S_CUTOFF,
+    S_HDR, S_REC, S_RECT, S_CNT, S_ZBITS, S_KEYA0, S_KEYA1, S_VALA0, S_VALA1, S_RECTS, S_BASE, S_BLK,
+    S_KEYC0, S_KEYC1, S_VALC0, S_VALC1, S_PARTIAL, S_HIST, S_BINTOT, S_RANGES, S_ORDER, S_CUTOFF,
     S_TFINAL, S_LAST, S_COUNT
 };
 const char* kSlotNames[S_COUNT] = {
-    "header", "records", "rect", "count", "keys_a0", "keys_a1", "vals_a0", "vals_a1",
+    "header", "records", "rect", "count", "zbits", "keys_a0", "keys_a1", "vals_a0", "vals_a1",
     "rect_sorted", "base", "block_sums", "keys_c0", "keys_c1", "vals_c0", "vals_c1",
-    "partial", "hist", "bin_total", "ranges", "cutoff", "t_final", "last"};
+    "partial", "hist", "bin_total", "ranges", "tile_order", "cutoff", "t_final", "last"};
 
 struct Plan {
     ViewTable vt;
@@ -161,6 +161,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     pl.bytes[S_REC] = (size_t)N * vt.rec_words * 4;
     pl.bytes[S_RECT] = (size_t)N * 8;
     pl.bytes[S_CNT] = (size_t)N * 4;
+    pl.bytes[S_ZBITS] = (size_t)N * 4;
     pl.bytes[S_KEYA0] = pl.bytes[S_KEYA1] = pl.bytes[S_VALA0] = pl.bytes[S_VALA1] = (size_t)N * 4;
     pl.bytes[S_RECTS] = (size_t)N * 8;
     pl.bytes[S_BASE] = (size_t)N * 4;
@@ -170,6 +171,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     pl.bytes[S_HIST] = (size_t)512 * pl.hist_tiles * 4;
     pl.bytes[S_BINTOT] = (size_t)512 * 8 * 4;
     pl.bytes[S_RANGES] = (size_t)ntile * 8;
+    pl.bytes[S_ORDER] = (size_t)ntile * 4;
     pl.bytes[S_CUTOFF] = (size_t)ntile * 8;
     pl.bytes[S_TFINAL] = (size_t)npix * 4;
     pl.bytes[S_LAST] = (size_t)npix * 4;
@@ -191,6 +193,7 @@ Bufs make_bufs(const Plan& pl, void* ws) {
     b.rec = (uint32_t*)at(S_REC);
     b.rect = (uint2*)at(S_RECT);
     b.cnt = (uint32_t*)at(S_CNT);
+    b.zbits = (uint32_t*)at(S_ZBITS);
     b.keyA[0] = (uint32_t*)at(S_KEYA0);
     b.keyA[1] = (uint32_t*)at(S_KEYA1);
     b.valA[0] = (uint32_t*)at(S_VALA0);
@@ -206,6 +209,7 @@ Bufs make_bufs(const Plan& pl, void* ws) {
     b.hist = (uint32_t*)at(S_HIST);
     b.bin_total = (uint32_t*)at(S_BINTOT);
     b.ranges = (uint2*)at(S_RANGES);
+    b.order = (uint32_t*)at(S_ORDER);
     b.cutoff = (uint2*)at(S_CUTOFF);
     b.t_final = (float*)at(S_TFINAL);
     b.last = (uint32_t*)at(S_LAST);
@@ -222,6 +226,7 @@ __global__ void k_init_header(WsHeader* h, int32_t n_views, long long n_points, 
     h->n_copies_raw = 0u;
     h->n_views = (uint32_t)n_views;
     h->needed = 0ull;
+    h->needed_bwd = 0ull;
     h->n_points = n_points;
     h->copy_cap = cap;
     h->n_tiles = n_tiles;
@@ -254,23 +259,24 @@ struct Profiler {
 };
 Profiler g_prof;
 
-struct Stage {
-    cudaStream_t s;
-    int idx = -1;
-    Stage(const char* name, cudaStream_t st) : s(st) {
-        std::lock_guard<std::mutex> lk(g_prof.mu);
-        if (!g_prof.on) return;
-        ProfRec r{name, g_prof.get(), g_prof.get()};
-        cudaEventRecord(r.a, s);
-        g_prof.recs.push_back(r);
-        idx = (int)g_prof.recs.size() - 1;
-    }
-    ~Stage() {
-        if (idx < 0) return;
-        std::lock_guard<std::mutex> lk(g_prof.mu);
-        if (idx < (int)g_prof.recs.size()) cudaEventRecord(g_prof.recs[idx].b, s);
-    }
-};
+}  // namespace
+
+ProfScope::ProfScope(const char* name, cudaStream_t st) : idx(-1), s(st) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!g_prof.on) return;
+    ProfRec r{name, g_prof.get(), g_prof.get()};
+    cudaEventRecord(r.a, s);
+    g_prof.recs.push_back(r);
+    idx = (int)g_prof.recs.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+    if (idx < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (idx < (int)g_prof.recs.size()) cudaEventRecord(g_prof.recs[idx].b, s);
+}
+
+namespace {
 
 #define RAST_TRY(expr)                      \
     do {                                    \
@@ -278,64 +284,46 @@ struct Stage {
         if (e_ != cudaSuccess) return e_;   \
     } while (0)
 
+const char* const kDepthSortNames[3] = {"depth_sort.hist", "depth_sort.scan", "depth_sort.scatter"};
+const char* const kTileSortNames[3] = {"tile_sort.hist", "tile_sort.scan", "tile_sort.scatter"};
+
 cudaError_t run_fwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
     const ViewTable& vt = pl.vt;
     {
-        Stage st("init", s);
+        ProfScope ps("init_header", s);
         k_init_header<<<1, 1, 0, s>>>(b.hdr, vt.n_views, vt.n_total, pl.copy_cap, vt.tiles_total,
                                       vt.pix_total);
         RAST_TRY(cudaGetLastError());
     }
-    {
-        Stage st("project", s);
-        RAST_TRY(launch_project(vt, b, s));
-    }
+    RAST_TRY(launch_project(vt, b, s));
     int ra = 0, rc = 0;
     {
-        Stage st("sort_depth", s);
         uint32_t* k[2] = {b.keyA[0], b.keyA[1]};
         uint32_t* v[2] = {b.valA[0], b.valA[1]};
         RAST_TRY(radix_sort(k, v, vt.n_total, nullptr, vt.n_total, pl.planA, b.hist, b.hist_tiles,
-                            b.bin_total, s, &ra));
+                            b.bin_total, s, &ra, kDepthSortNames));
     }
     const uint32_t* depth_sorted = b.valA[ra];
+    RAST_TRY(launch_duplicate(vt, b, depth_sorted, s));
     {
-        Stage st("duplicate", s);
-        RAST_TRY(launch_duplicate(vt, b, depth_sorted, s));
-    }
-    {
-        Stage st("sort_tile", s);
         uint32_t* k[2] = {b.keyC[0], b.keyC[1]};
         uint32_t* v[2] = {b.valC[0], b.valC[1]};
         RAST_TRY(radix_sort(k, v, 0, &b.hdr->n_copies, pl.copy_cap, pl.planC, b.hist, b.hist_tiles,
-                            b.bin_total, s, &rc));
+                            b.bin_total, s, &rc, kTileSortNames));
     }
-    {
-        Stage st("ranges", s);
-        RAST_TRY(launch_ranges(vt, b, b.keyC[rc], s));
-    }
-    {
-        Stage st("blend_fwd", s);
-        RAST_TRY(launch_blend_fwd(vt, b, b.valC[rc], s));
-    }
+    RAST_TRY(launch_ranges(vt, b, b.keyC[rc], s));
+    RAST_TRY(launch_tile_order(vt, b, s));
+    RAST_TRY(launch_blend_fwd(vt, b, b.valC[rc], s));
     return cudaSuccess;
 }
 
 cudaError_t run_bwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
     const ViewTable& vt = pl.vt;
     const int rc = pl.planC.passes & 1;
-    {
-        Stage st("point_scan", s);
-        RAST_TRY(launch_point_scan(vt, b, s));
-    }
-    {
-        Stage st("blend_bwd", s);
-        RAST_TRY(launch_blend_bwd(vt, b, b.valC[rc], s));
-    }
-    {
-        Stage st("reduce_grads", s);
-        RAST_TRY(launch_reduce_grads(vt, b, s));
-    }
+    RAST_TRY(cudaMemsetAsync(&b.hdr->needed_bwd, 0, sizeof(unsigned long long), s));
+    RAST_TRY(launch_point_scan(vt, b, s));
+    RAST_TRY(launch_blend_bwd(vt, b, b.valC[rc], s));
+    RAST_TRY(launch_reduce_grads(vt, b, s));
     return cudaSuccess;
 }
 
@@ -457,6 +445,7 @@ rast_status_t rasterize_get_status(const void* workspace, size_t ws_bytes, void*
         stats->needed_records = (int64_t)h.needed;
         stats->n_tiles = h.n_tiles;
         stats->n_pixels = h.n_pixels;
+        stats->needed_records_bwd = (int64_t)h.needed_bwd;
     }
     return r;
 }

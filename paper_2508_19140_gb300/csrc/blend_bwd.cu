@@ -25,11 +25,6 @@
 namespace rast {
 namespace {
 
-__device__ __forceinline__ uint32_t rect_rank(uint2 r, int tx, int ty) {
-    const int tx0 = r.x & 0xffff, ty0 = r.x >> 16, tx1 = r.y & 0xffff;
-    return (uint32_t)((ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0));
-}
-
 __device__ __forceinline__ uint32_t block_max_u32(uint32_t x, uint32_t* s) {
     if (threadIdx.x == 0) *s = 0;
     __syncthreads();
@@ -44,10 +39,11 @@ __device__ __forceinline__ uint32_t block_max_u32(uint32_t x, uint32_t* s) {
 
 template <int C, bool BF16>
 __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
-    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pts,
-    const uint32_t* __restrict__ rec, const float* __restrict__ t_final,
-    const uint32_t* __restrict__ last_in, const uint32_t* __restrict__ base,
-    const uint2* __restrict__ rect, float* __restrict__ partial, uint2* __restrict__ cutoff) {
+    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec,
+    const float* __restrict__ t_final, const uint32_t* __restrict__ last_in,
+    const uint32_t* __restrict__ base, float* __restrict__ partial, uint2* __restrict__ cutoff,
+    WsHeader* __restrict__ hdr) {
     constexpr int P = C + 1;  // dfeat[C], dopacity
     __shared__ float s_a[kBatch], s_b[kBatch], s_o[kBatch], s_z[kBatch];
     __shared__ int s_i0[kBatch], s_j0[kBatch];
@@ -56,7 +52,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     extern __shared__ float s_contrib[];  // [4 slots][P][kBatch]
     __shared__ uint32_t s_red;
 
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = order[blockIdx.x];
     const ViewDev& V = vt.v[view_of_tile(vt, tile)];
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
@@ -82,6 +78,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
         if (V.g_depth) gD = V.g_depth[pix];
     }
     const uint32_t maxlast = block_max_u32(last, &s_red);
+    if (tid == 0 && maxlast) atomicAdd(&hdr->needed_bwd, (unsigned long long)maxlast);
     if (maxlast == 0) {
         if (tid == 0) cutoff[tile] = make_uint2(0u, 0u);
         return;
@@ -90,21 +87,35 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
     float Sg = 0.f, SD = 0.f;
     const float Kd = -gA * Tfin;  // constant part of the 1/(1-a) term
+    const uint32_t end = rg.x + maxlast;
+    const int nb = (int)((maxlast - 1) / kBatch);
 
-    for (int bi = (int)((maxlast - 1) / kBatch); bi >= 0; --bi) {
-        const uint32_t rel0 = (uint32_t)bi * kBatch;
-        const uint32_t b0 = rg.x + rel0;
-        const uint32_t bend = rg.x + maxlast < b0 + kBatch ? rg.x + maxlast : b0 + kBatch;
-        const uint32_t q = b0 + tid;
-#pragma unroll
-        for (int k = 0; k < 4 * P; ++k) s_contrib[k * kBatch + tid] = 0.f;
-        uint32_t gi = 0;
-        if (q < bend) {
+    // Prologue: records (+ slot base) of the last batch, indices of the one before.
+    uint4 g = make_uint4(0u, 0u, 0u, 0u);
+    float f[C];
+    uint32_t gi = 0, bs = 0;
+    {
+        const uint32_t q = rg.x + (uint32_t)nb * kBatch + tid;
+        if (q < end) {
             gi = pts[q];
             const uint32_t* rp = rec + (size_t)gi * RW;
-            const uint4 g = *reinterpret_cast<const uint4*>(rp);
-            float f[C];
+            g = *reinterpret_cast<const uint4*>(rp);
             load_features<C, BF16>(rp + FW, f);
+            bs = base[gi];
+        }
+    }
+    uint32_t gi_next = (nb > 0) ? pts[rg.x + (uint32_t)(nb - 1) * kBatch + tid] : 0u;
+
+    for (int bi = nb; bi >= 0; --bi) {
+        const uint32_t rel0 = (uint32_t)bi * kBatch;
+        const uint32_t b0 = rg.x + rel0;
+        const uint32_t q = b0 + tid;
+        const bool have = q < end;
+#pragma unroll
+        for (int k = 0; k < 4 * P; ++k) s_contrib[k * kBatch + tid] = 0.f;
+        int slot_base = 0, slot_w = 1, rtx = 0, rty = 0;
+        uint32_t my_gi = gi, my_bs = bs;
+        if (have) {
             const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
             s_a[tid] = bg.a;
             s_b[tid] = bg.b;
@@ -126,9 +137,27 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
                     if ((unsigned)X < (unsigned)kTile) atomicOr(&s_mask[Y * kTile + X][warp], bit);
                 }
             }
-            if (q + 1 == rg.x + maxlast) cutoff[tile] = make_uint2(g.z, gi);
+            // The point's tile rect (as the projection computed it) and this tile's rank in it.
+            const int tx0 = max(bg.i0, 0) / kTile, tx1 = min(bg.i0 + 1, V.W - 1) / kTile;
+            const int ty0 = max(bg.j0, 0) / kTile;
+            slot_w = tx1 - tx0 + 1;
+            rtx = tx - tx0;
+            rty = ty - ty0;
+            slot_base = rty * slot_w + rtx;
+            if (q + 1 == end) cutoff[tile] = make_uint2(g.z, gi);
         }
         __syncthreads();
+        // Prefetch the previous batch (records + slot bases) and the indices before it.
+        if (bi > 0) {
+            const uint32_t qp = b0 - kBatch + tid;
+            gi = gi_next;
+            const uint32_t* rp = rec + (size_t)gi * RW;
+            g = *reinterpret_cast<const uint4*>(rp);
+            load_features<C, BF16>(rp + FW, f);
+            bs = base[gi];
+            (void)qp;
+            gi_next = (bi > 1) ? pts[b0 - 2 * kBatch + tid] : 0u;
+        }
         if (inside && last > rel0) {
 #pragma unroll 1
             for (int w = 7; w >= 0; --w) {
@@ -142,13 +171,13 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
                     const float wgt = bilin_weight(px, py, i0, j0, s_a[r], s_b[r]);
                     const float ow = __fmul_rn(s_o[r], wgt);
                     const float alpha = fminf(ow, amax);
-                    const float om = __fsub_rn(1.f, alpha);
-                    const float Tk = __fdiv_rn(T, om);
+                    const float inv = __frcp_rn(__fsub_rn(1.f, alpha));
+                    const float Tk = T * inv;
                     float fdot = 0.f;
 #pragma unroll
                     for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], s_f[c][r], fdot);
                     const float z = s_z[r];
-                    const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) / om;
+                    const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) * inv;
                     const float ta = Tk * alpha;
                     Sg = fmaf(ta, fdot, Sg);
                     SD = fmaf(ta, z, SD);
@@ -164,15 +193,16 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
 #pragma unroll
         for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
         __syncthreads();
-        if (q < bend) {
-            const uint2 rc = rect[gi];
-            float* out = partial + (size_t)(base[gi] + rect_rank(rc, tx, ty)) * P;
+        if (have) {
+            float* out = partial + (size_t)(my_bs + (uint32_t)slot_base) * P;
 #pragma unroll
             for (int k = 0; k < P; ++k) {
                 const float* cb = s_contrib + k * kBatch + tid;
                 out[k] = ((cb[0] + cb[P * kBatch]) + cb[2 * P * kBatch]) + cb[3 * P * kBatch];
             }
         }
+        (void)my_gi;
+        (void)rty;
         __syncthreads();
     }
 }
@@ -189,10 +219,11 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 template <int C, bool BF16>
 __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
-    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pts,
-    const uint32_t* __restrict__ rec, const float* __restrict__ t_final,
-    const uint32_t* __restrict__ last_in, const uint32_t* __restrict__ base,
-    const uint2* __restrict__ rect, float* __restrict__ partial, uint2* __restrict__ cutoff) {
+    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec,
+    const float* __restrict__ t_final, const uint32_t* __restrict__ last_in,
+    const uint32_t* __restrict__ base, float* __restrict__ partial, uint2* __restrict__ cutoff,
+    WsHeader* __restrict__ hdr) {
     constexpr int P = C + 7;  // dfeat[C], do, du, dv, dca, dcb, dcc, dz
     __shared__ float s_um[kGBatch], s_vm[kGBatch], s_o[kGBatch], s_z[kGBatch];
     __shared__ float s_ca[kGBatch], s_cb[kGBatch], s_cc[kGBatch];
@@ -201,7 +232,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
     extern __shared__ float s_contrib[];  // [8 warps][P][kGBatch]
     __shared__ uint32_t s_red;
 
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = order[blockIdx.x];
     const ViewDev& V = vt.v[view_of_tile(vt, tile)];
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
@@ -229,28 +260,43 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
         if (V.g_depth) gD = V.g_depth[pix];
     }
     const uint32_t maxlast = block_max_u32(last, &s_red);
+    if (tid == 0 && maxlast) atomicAdd(&hdr->needed_bwd, (unsigned long long)maxlast);
     if (maxlast == 0) {
         if (tid == 0) cutoff[tile] = make_uint2(0u, 0u);
         return;
     }
     float Sg = 0.f, SD = 0.f;
     const float Kd = -gA * Tfin;
+    const uint32_t end = rg.x + maxlast;
+    const int nb = (int)((maxlast - 1) / kGBatch);
+    const bool loader = tid < kGBatch;
 
-    for (int bi = (int)((maxlast - 1) / kGBatch); bi >= 0; --bi) {
-        const uint32_t rel0 = (uint32_t)bi * kGBatch;
-        const uint32_t b0 = rg.x + rel0;
-        const uint32_t bend = rg.x + maxlast < b0 + kGBatch ? rg.x + maxlast : b0 + kGBatch;
-        const int nrec = (int)(bend - b0);
-        for (int k = tid; k < 8 * P * kGBatch; k += kBlendThreads) s_contrib[k] = 0.f;
-        uint32_t gi = 0;
-        const uint32_t q = b0 + tid;
-        if (tid < kGBatch && q < bend) {
+    uint4 g = make_uint4(0u, 0u, 0u, 0u), h = make_uint4(0u, 0u, 0u, 0u);
+    float f[C];
+    uint32_t gi = 0, bs = 0;
+    if (loader) {
+        const uint32_t q = rg.x + (uint32_t)nb * kGBatch + tid;
+        if (q < end) {
             gi = pts[q];
             const uint32_t* rp = rec + (size_t)gi * RW;
-            const uint4 g = *reinterpret_cast<const uint4*>(rp);
-            const uint4 h = *reinterpret_cast<const uint4*>(rp + 4);
-            float f[C];
+            g = *reinterpret_cast<const uint4*>(rp);
+            h = *reinterpret_cast<const uint4*>(rp + 4);
             load_features<C, BF16>(rp + FW, f);
+            bs = base[gi];
+        }
+    }
+    uint32_t gi_next = (loader && nb > 0) ? pts[rg.x + (uint32_t)(nb - 1) * kGBatch + tid] : 0u;
+
+    for (int bi = nb; bi >= 0; --bi) {
+        const uint32_t rel0 = (uint32_t)bi * kGBatch;
+        const uint32_t b0 = rg.x + rel0;
+        const uint32_t bend = end < b0 + kGBatch ? end : b0 + kGBatch;
+        const int nrec = (int)(bend - b0);
+        for (int k = tid; k < 8 * P * kGBatch; k += kBlendThreads) s_contrib[k] = 0.f;
+        const bool have = loader && b0 + tid < bend;
+        const uint32_t my_bs = bs;
+        int slot = 0;
+        if (have) {
             const float um = __fsub_rn(__uint_as_float(g.x), 0.5f);
             const float vm = __fsub_rn(__uint_as_float(g.y), 0.5f);
             const GaussBox bx = gauss_box(um, vm, __uint_as_float(h.w));
@@ -264,9 +310,22 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
             s_box[tid] = make_int4(bx.x0, bx.x1, bx.y0, bx.y1);
 #pragma unroll
             for (int c = 0; c < C; ++c) s_f[c][tid] = f[c];
-            if (q + 1 == rg.x + maxlast) cutoff[tile] = make_uint2(g.z, gi);
+            // tile rect of the in-image box, as the projection computed it
+            const int tx0 = max(bx.x0, 0) / kTile, tx1 = min(bx.x1, V.W - 1) / kTile;
+            const int ty0 = max(bx.y0, 0) / kTile;
+            slot = (ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0);
+            if (b0 + tid + 1 == end) cutoff[tile] = make_uint2(g.z, gi);
         }
         __syncthreads();
+        if (loader && bi > 0) {
+            gi = gi_next;
+            const uint32_t* rp = rec + (size_t)gi * RW;
+            g = *reinterpret_cast<const uint4*>(rp);
+            h = *reinterpret_cast<const uint4*>(rp + 4);
+            load_features<C, BF16>(rp + FW, f);
+            bs = base[gi];
+            gi_next = (bi > 1) ? pts[b0 - 2 * kGBatch + tid] : 0u;
+        }
         const uint32_t wmax = __reduce_max_sync(0xffffffffu, last);
         if (wmax > rel0) {
 #pragma unroll 1
@@ -302,13 +361,13 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
                         const float o = s_o[r];
                         const float og = __fmul_rn(o, G);
                         const float alpha = fminf(og, amax);
-                        const float om = __fsub_rn(1.f, alpha);
-                        const float Tk = __fdiv_rn(T, om);
+                        const float inv = __frcp_rn(__fsub_rn(1.f, alpha));
+                        const float Tk = T * inv;
                         float fdot = 0.f;
 #pragma unroll
                         for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], s_f[c][r], fdot);
                         const float z = s_z[r];
-                        const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) / om;
+                        const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) * inv;
                         const float ta = Tk * alpha;
                         Sg = fmaf(ta, fdot, Sg);
                         SD = fmaf(ta, z, SD);
@@ -337,9 +396,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
             }
         }
         __syncthreads();
-        if (tid < kGBatch && q < bend) {
-            const uint2 rc = rect[gi];
-            float* out = partial + (size_t)(base[gi] + rect_rank(rc, tx, ty)) * P;
+        if (have) {
+            float* out = partial + (size_t)(my_bs + (uint32_t)slot) * P;
 #pragma unroll
             for (int k = 0; k < P; ++k) {
                 float acc = 0.f;
@@ -355,7 +413,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
 // ---------------------------------------------------------------- K8 reduce
 
 template <int C, int MODE>
-__global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const uint32_t* __restrict__ rec,
+__global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const uint32_t* __restrict__ zbits,
                                                       const uint2* __restrict__ rect,
                                                       const uint32_t* __restrict__ base,
                                                       const uint2* __restrict__ cutoff,
@@ -371,7 +429,7 @@ __global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const 
     const uint2 rc = rect[gi];
     const uint32_t cnt = rect_count(rc);
     if (cnt) {
-        const uint32_t zb = rec[(size_t)gi * vt.rec_words + 2];
+        const uint32_t zb = zbits[gi];
         const int tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff, ty1 = rc.y >> 16;
         const float* pp = partial + (size_t)base[gi] * P;
         int k = 0;
@@ -478,8 +536,9 @@ cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts
             if (e != cudaSuccess) return e;
             set = true;
         }
+        ProfScope ps("blend_bwd", s);
         k_blend_bwd_bilinear<C, BF16><<<grid, kBlendThreads, smem, s>>>(
-            vt, b.ranges, pts, b.rec, b.t_final, b.last, b.base, b.rect, b.partial, b.cutoff);
+            vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.cutoff, b.hdr);
     } else {
         constexpr size_t smem = sizeof(float) * 8 * (C + 7) * kGBatch;
         static bool set = false;
@@ -489,8 +548,9 @@ cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts
             if (e != cudaSuccess) return e;
             set = true;
         }
+        ProfScope ps("blend_bwd", s);
         k_blend_bwd_gauss<C, BF16><<<grid, kBlendThreads, smem, s>>>(
-            vt, b.ranges, pts, b.rec, b.t_final, b.last, b.base, b.rect, b.partial, b.cutoff);
+            vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.cutoff, b.hdr);
     }
     return cudaGetLastError();
 }
@@ -503,10 +563,11 @@ cudaError_t launch_bwd_c(const ViewTable& vt, const Bufs& b, const uint32_t* pts
 template <int C>
 cudaError_t launch_reduce_c(const ViewTable& vt, const Bufs& b, cudaStream_t s) {
     const unsigned grid = (unsigned)((vt.n_total + 255) / 256);
+    ProfScope ps("reduce_grads", s);
     if (vt.mode == 0)
-        k_reduce_grads<C, 0><<<grid, 256, 0, s>>>(vt, b.rec, b.rect, b.base, b.cutoff, b.partial);
+        k_reduce_grads<C, 0><<<grid, 256, 0, s>>>(vt, b.zbits, b.rect, b.base, b.cutoff, b.partial);
     else
-        k_reduce_grads<C, 1><<<grid, 256, 0, s>>>(vt, b.rec, b.rect, b.base, b.cutoff, b.partial);
+        k_reduce_grads<C, 1><<<grid, 256, 0, s>>>(vt, b.zbits, b.rect, b.base, b.cutoff, b.partial);
     return cudaGetLastError();
 }
 

@@ -5,8 +5,11 @@
 // fragments in (depth, point index) order, stopping before the first fragment
 // that would take T below t_min. Each CTA walks its tile's sorted list in
 // batches of 256 records: every thread gathers one record (two or three
-// 128-bit loads of a 16-byte aligned record) into shared memory, then each
-// pixel composites the records of the batch that cover it, in list order.
+// 128-bit loads of a 16-byte aligned record) and stages it in shared memory,
+// then each pixel composites the records of the batch that cover it, in list
+// order. The loads of batch b+1 (and the point indices of batch b+2) are issued
+// before batch b is composited, so the gather latency overlaps the compositing
+// instead of adding to every batch of the tile's serial chain.
 //
 // Bilinear splats touch at most 4 pixels, so testing every record against
 // every pixel (256 tests per record) would make the kernel ALU-bound. Instead
@@ -18,6 +21,8 @@
 // ballots the batch's records whose pixel box overlaps the sub-tile, and
 // composites only those, all 32 lanes in lockstep.
 //
+// Tiles are visited heaviest first (k_tile_order): the blend's duration is
+// bounded below by its longest tile list, so that list must start at once.
 // The CTA stops reading as soon as every in-image pixel has terminated
 // (__syncthreads_count), which is where early termination saves HBM traffic.
 // Saved for the backward pass: T_final and the 1-based list position of the
@@ -29,18 +34,49 @@
 namespace rast {
 namespace {
 
+// Tiles in descending order of list length, bucketed by floor(log2(len)).
+// One CTA; the order inside a bucket is arbitrary and only affects scheduling.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, int64_t P,
+                                                     uint32_t* __restrict__ order) {
+    __shared__ uint32_t s_cnt[33];
+    __shared__ uint32_t s_off[33];
+    if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < P; t += 1024) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y - r.x;
+        const int bk = len ? 32 - __clz(len) : 0;  // 0..32
+        atomicAdd(&s_cnt[bk], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int bk = 32; bk >= 0; --bk) {
+            s_off[bk] = run;
+            run += s_cnt[bk];
+        }
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < P; t += 1024) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y - r.x;
+        const int bk = len ? 32 - __clz(len) : 0;
+        order[atomicAdd(&s_off[bk], 1u)] = (uint32_t)t;
+    }
+}
+
 template <int C, bool BF16>
 __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
-    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pts,
-    const uint32_t* __restrict__ rec, float* __restrict__ t_final, uint32_t* __restrict__ last_out,
-    WsHeader* __restrict__ hdr) {
+    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec, float* __restrict__ t_final,
+    uint32_t* __restrict__ last_out, WsHeader* __restrict__ hdr) {
     __shared__ float s_a[kBatch], s_b[kBatch], s_o[kBatch], s_z[kBatch];
     __shared__ int s_i0[kBatch], s_j0[kBatch];
     __shared__ float s_f[C][kBatch];
     __shared__ uint32_t s_mask[kTilePix][9];  // 8 words + 1 pad: conflict-free row reads
     __shared__ uint32_t s_maxstop;
 
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = order[blockIdx.x];
     const ViewDev& V = vt.v[view_of_tile(vt, tile)];
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
@@ -61,15 +97,22 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
     for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
     if (tid == 0) s_maxstop = 0;
 
-    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBatch) {
-        if (__syncthreads_count(!done) == 0) break;
-        const uint32_t q = b0 + tid;
+    // Prologue: records of batch 0 and indices of batch 1 in flight.
+    uint4 g = make_uint4(0u, 0u, 0u, 0u);
+    float f[C];
+    {
+        const uint32_t q = rg.x + tid;
         if (q < rg.y) {
-            const uint32_t gi = pts[q];
-            const uint32_t* rp = rec + (size_t)gi * RW;
-            const uint4 g = *reinterpret_cast<const uint4*>(rp);
-            float f[C];
+            const uint32_t* rp = rec + (size_t)pts[q] * RW;
+            g = *reinterpret_cast<const uint4*>(rp);
             load_features<C, BF16>(rp + FW, f);
+        }
+    }
+    uint32_t gi_next = (rg.x + kBatch + tid < rg.y) ? pts[rg.x + kBatch + tid] : 0u;
+    __syncthreads();
+
+    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBatch) {
+        if (b0 + tid < rg.y) {
             const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
             s_a[tid] = bg.a;
             s_b[tid] = bg.b;
@@ -92,7 +135,17 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
                 }
             }
         }
-        __syncthreads();
+        if (__syncthreads_count(!done) == 0) break;
+        // Prefetch: records of the next batch, indices of the one after.
+        {
+            const uint32_t qn = b0 + kBatch + tid;
+            if (qn < rg.y) {
+                const uint32_t* rp = rec + (size_t)gi_next * RW;
+                g = *reinterpret_cast<const uint4*>(rp);
+                load_features<C, BF16>(rp + FW, f);
+            }
+            gi_next = (qn + kBatch < rg.y) ? pts[qn + kBatch] : 0u;
+        }
         if (!done) {
             const uint32_t rel0 = b0 - rg.x;
 #pragma unroll 1
@@ -121,13 +174,20 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
         }
 #pragma unroll
         for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
+        __syncthreads();
     }
 
     if (inside) {
         const int64_t pix = (int64_t)py * V.W + px;
         float* of = V.out_feat + pix * C;
+        if (C % 4 == 0) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) of[c] = F[c];
+            for (int c = 0; c < C; c += 4)
+                *reinterpret_cast<float4*>(of + c) = make_float4(F[c], F[c + 1], F[c + 2], F[c + 3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) of[c] = F[c];
+        }
         if (V.out_alpha) V.out_alpha[pix] = A;
         if (V.out_depth) V.out_depth[pix] = Dp;
         t_final[V.pix_off + pix] = T;
@@ -144,16 +204,16 @@ constexpr int kGroups = kBatch / 32;
 
 template <int C, bool BF16>
 __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
-    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pts,
-    const uint32_t* __restrict__ rec, float* __restrict__ t_final, uint32_t* __restrict__ last_out,
-    WsHeader* __restrict__ hdr) {
+    const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec, float* __restrict__ t_final,
+    uint32_t* __restrict__ last_out, WsHeader* __restrict__ hdr) {
     __shared__ float s_um[kBatch], s_vm[kBatch], s_o[kBatch], s_z[kBatch];
     __shared__ float s_ca[kBatch], s_cb[kBatch], s_cc[kBatch];
     __shared__ int4 s_box[kBatch];
     __shared__ float s_f[C][kBatch];
     __shared__ uint32_t s_maxstop;
 
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = order[blockIdx.x];
     const ViewDev& V = vt.v[view_of_tile(vt, tile)];
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
@@ -175,16 +235,22 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
     bool done = !inside;
     if (tid == 0) s_maxstop = 0;
 
-    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBatch) {
-        if (__syncthreads_count(!done) == 0) break;
-        const uint32_t q = b0 + tid;
+    uint4 g = make_uint4(0u, 0u, 0u, 0u), h = make_uint4(0u, 0u, 0u, 0u);
+    float f[C];
+    {
+        const uint32_t q = rg.x + tid;
         if (q < rg.y) {
-            const uint32_t gi = pts[q];
-            const uint32_t* rp = rec + (size_t)gi * RW;
-            const uint4 g = *reinterpret_cast<const uint4*>(rp);
-            const uint4 h = *reinterpret_cast<const uint4*>(rp + 4);
-            float f[C];
+            const uint32_t* rp = rec + (size_t)pts[q] * RW;
+            g = *reinterpret_cast<const uint4*>(rp);
+            h = *reinterpret_cast<const uint4*>(rp + 4);
             load_features<C, BF16>(rp + FW, f);
+        }
+    }
+    uint32_t gi_next = (rg.x + kBatch + tid < rg.y) ? pts[rg.x + kBatch + tid] : 0u;
+    __syncthreads();
+
+    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBatch) {
+        if (b0 + tid < rg.y) {
             const float um = __fsub_rn(__uint_as_float(g.x), 0.5f);
             const float vm = __fsub_rn(__uint_as_float(g.y), 0.5f);
             const GaussBox bx = gauss_box(um, vm, __uint_as_float(h.w));
@@ -199,7 +265,17 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
 #pragma unroll
             for (int c = 0; c < C; ++c) s_f[c][tid] = f[c];
         }
-        __syncthreads();
+        if (__syncthreads_count(!done) == 0) break;
+        {
+            const uint32_t qn = b0 + kBatch + tid;
+            if (qn < rg.y) {
+                const uint32_t* rp = rec + (size_t)gi_next * RW;
+                g = *reinterpret_cast<const uint4*>(rp);
+                h = *reinterpret_cast<const uint4*>(rp + 4);
+                load_features<C, BF16>(rp + FW, f);
+            }
+            gi_next = (qn + kBatch < rg.y) ? pts[qn + kBatch] : 0u;
+        }
         const int nrec = (int)min((uint32_t)kBatch, rg.y - b0);
         const uint32_t rel0 = b0 - rg.x;
         if (!__all_sync(0xffffffffu, done)) {
@@ -243,6 +319,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
                 if (__all_sync(0xffffffffu, done)) break;
             }
         }
+        __syncthreads();
     }
 
     if (inside) {
@@ -265,11 +342,12 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
 template <int C, bool BF16>
 cudaError_t launch_fwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     const unsigned grid = (unsigned)vt.tiles_total;
+    ProfScope ps("blend_fwd", s);
     if (vt.mode == 0)
-        k_blend_fwd_bilinear<C, BF16><<<grid, kBlendThreads, 0, s>>>(vt, b.ranges, pts, b.rec,
+        k_blend_fwd_bilinear<C, BF16><<<grid, kBlendThreads, 0, s>>>(vt, b.ranges, b.order, pts, b.rec,
                                                                      b.t_final, b.last, b.hdr);
     else
-        k_blend_fwd_gauss<C, BF16><<<grid, kBlendThreads, 0, s>>>(vt, b.ranges, pts, b.rec,
+        k_blend_fwd_gauss<C, BF16><<<grid, kBlendThreads, 0, s>>>(vt, b.ranges, b.order, pts, b.rec,
                                                                   b.t_final, b.last, b.hdr);
     return cudaGetLastError();
 }
@@ -283,6 +361,13 @@ cudaError_t launch_fwd_c(const ViewTable& vt, const Bufs& b, const uint32_t* pts
 
 bool channels_supported(int C) {
     return C == 1 || C == 2 || C == 3 || C == 4 || C == 8 || C == 16;
+}
+
+cudaError_t launch_tile_order(const ViewTable& vt, const Bufs& b, cudaStream_t s) {
+    if (vt.tiles_total == 0) return cudaSuccess;
+    ProfScope ps("tile_order", s);
+    k_tile_order<<<1, 1024, 0, s>>>(b.ranges, vt.tiles_total, b.order);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_blend_fwd(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {

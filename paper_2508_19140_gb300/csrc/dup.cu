@@ -91,15 +91,17 @@ __global__ void __launch_bounds__(kT) k_count_blocks(const uint32_t* __restrict_
 __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ blk, int64_t nb,
                                                       WsHeader* hdr, int64_t cap) {
     __shared__ uint32_t s_warp[32];
-    __shared__ unsigned long long s_total;
-    if (threadIdx.x == 0) s_total = 0ull;
-    __syncthreads();
+    __shared__ unsigned long long s_wtot[32];
     const int64_t per = (nb + 1023) / 1024;
     const int64_t lo = threadIdx.x * per;
     const int64_t hi = lo + per < nb ? lo + per : nb;
     unsigned long long s = 0;
     for (int64_t t = lo; t < hi; ++t) s += blk[t];
-    atomicAdd(&s_total, s);
+    // 64-bit total: warp shuffle reduction, then one value per warp
+    unsigned long long ws = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+    if ((threadIdx.x & 31) == 0) s_wtot[threadIdx.x >> 5] = ws;
     uint32_t tot;
     uint32_t run = block_excl_scan<1024>((uint32_t)s, s_warp, tot);  // exact whenever total <= cap
     for (int64_t t = lo; t < hi; ++t) {
@@ -108,7 +110,8 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ blk
         run += c;
     }
     if (hdr && threadIdx.x == 0) {
-        const unsigned long long total = s_total;
+        unsigned long long total = 0;
+        for (int w = 0; w < 32; ++w) total += s_wtot[w];
         const bool over = total > (unsigned long long)cap;
         hdr->n_copies_raw = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
         hdr->n_copies = over ? 0u : (uint32_t)total;
@@ -198,10 +201,19 @@ cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t*
     const int64_t n = vt.n_total;
     const int64_t nb = (n + kScanItems - 1) / kScanItems;
     if (nb == 0) return cudaSuccess;  // the header was zeroed at the start of the pass
-    k_dup_count<<<(unsigned)nb, kT, 0, s>>>(sorted_pts, b.rect, b.rectS, n, b.blk);
-    k_scan_blocks<<<1, 1024, 0, s>>>(b.blk, nb, b.hdr, b.copy_cap);
-    k_dup_write<<<(unsigned)nb, kT, 0, s>>>(vt, sorted_pts, b.rectS, n, b.blk, b.keyC[0], b.valC[0],
-                                           b.copy_cap);
+    {
+        ProfScope ps("dup.count", s);
+        k_dup_count<<<(unsigned)nb, kT, 0, s>>>(sorted_pts, b.rect, b.rectS, n, b.blk);
+    }
+    {
+        ProfScope ps("dup.scan", s);
+        k_scan_blocks<<<1, 1024, 0, s>>>(b.blk, nb, b.hdr, b.copy_cap);
+    }
+    {
+        ProfScope ps("dup.write", s);
+        k_dup_write<<<(unsigned)nb, kT, 0, s>>>(vt, sorted_pts, b.rectS, n, b.blk, b.keyC[0],
+                                               b.valC[0], b.copy_cap);
+    }
     return cudaGetLastError();
 }
 
@@ -212,6 +224,7 @@ cudaError_t launch_ranges(const ViewTable& vt, const Bufs& b, const uint32_t* so
     int64_t g = (b.copy_cap + kT - 1) / kT;
     const int64_t gmax = (int64_t)sm_count() * 8;
     if (g > gmax) g = gmax;
+    ProfScope ps("ranges", s);
     k_ranges<<<(unsigned)g, kT, 0, s>>>(sorted_tiles, b.hdr, b.ranges);
     return cudaGetLastError();
 }
@@ -220,9 +233,18 @@ cudaError_t launch_point_scan(const ViewTable& vt, const Bufs& b, cudaStream_t s
     const int64_t n = vt.n_total;
     const int64_t nb = (n + kScanItems - 1) / kScanItems;
     if (nb == 0) return cudaSuccess;
-    k_count_blocks<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk);
-    k_scan_blocks<<<1, 1024, 0, s>>>(b.blk, nb, nullptr, 0);
-    k_scan_apply<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk, b.base);
+    {
+        ProfScope ps("point_scan.count", s);
+        k_count_blocks<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk);
+    }
+    {
+        ProfScope ps("point_scan.scan", s);
+        k_scan_blocks<<<1, 1024, 0, s>>>(b.blk, nb, nullptr, 0);
+    }
+    {
+        ProfScope ps("point_scan.apply", s);
+        k_scan_apply<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk, b.base);
+    }
     return cudaGetLastError();
 }
 

@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs 
     b.valA[0][gi] = (uint32_t)gi;
     b.rect[gi] = rect;
     b.cnt[gi] = count;
+    b.zbits[gi] = __float_as_uint(zc);
 }
 
 }  // namespace
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs 
 cudaError_t launch_project(const ViewTable& vt, const Bufs& b, cudaStream_t s) {
     if (vt.n_total == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((vt.n_total + 255) / 256);
+    ProfScope ps("project", s);
     if (vt.mode == 0) k_project<0><<<grid, 256, 0, s>>>(vt, b);
     else k_project<1><<<grid, 256, 0, s>>>(vt, b);
     return cudaGetLastError();

@@ -67,9 +67,10 @@ struct WsHeader {
     uint32_t n_copies;        // D after the dup scan (clamped to capacity)
     uint32_t n_copies_raw;    // D before clamping
     uint32_t n_views;
-    unsigned long long needed;  // records the blend had to read
+    unsigned long long needed;      // records the forward blend had to read
+    unsigned long long needed_bwd;  // records the backward replay read
     long long n_points, copy_cap, n_tiles, n_pixels;
-    long long pad[3];
+    long long pad[2];
 };
 
 // ---- small device helpers --------------------------------------------------
@@ -107,6 +108,17 @@ __device__ __forceinline__ uint32_t rect_count(uint2 r) {
     return (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
 }
 
+// ---- per-kernel profiling (defined in api.cu) ------------------------------
+// While profiling is enabled, records a CUDA event pair on `s` around the
+// scope; rasterize_profile_read() sums the times per name. `name` must have
+// static storage duration.
+struct ProfScope {
+    ProfScope(const char* name, cudaStream_t s);
+    ~ProfScope();
+    int idx;
+    cudaStream_t s;
+};
+
 // ---- launchers (each defined in its own translation unit) ------------------
 
 struct Bufs {
@@ -114,6 +126,7 @@ struct Bufs {
     uint32_t* rec;        // records, rec_words per point
     uint2* rect;          // tile rect per point
     uint32_t* cnt;        // copies per point (point order)
+    uint32_t* zbits;      // FP32 bits of the view depth per point (backward bookkeeping)
     uint32_t* keyA[2];    // depth sort ping-pong
     uint32_t* valA[2];
     uint2* rectS;         // rects in depth order
@@ -128,6 +141,7 @@ struct Bufs {
     uint32_t* bin_total;  // [passes][512]
     // per tile / pixel
     uint2* ranges;
+    uint32_t* order;      // tiles, heaviest list first
     uint2* cutoff;        // backward: (depth bits, point) of the last record processed per tile
     float* t_final;
     uint32_t* last;
@@ -150,13 +164,16 @@ cudaError_t launch_project(const ViewTable& vt, const Bufs& b, cudaStream_t s);
 // Stable LSD radix sort of (key, val) pairs in keys[0]/vals[0] using keys[1]/vals[1]
 // as scratch; count from d_n (device) if non-null else n. Returns the index (0/1)
 // of the buffer that holds the result.
+// names: profiling names of the hist, scan and scatter kernels.
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n,
                        int64_t cap, const SortPlan& plan, uint32_t* hist, int64_t hist_tiles,
-                       uint32_t* bin_total, cudaStream_t s, int* result_buf);
+                       uint32_t* bin_total, cudaStream_t s, int* result_buf,
+                       const char* const names[3]);
 cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
                              cudaStream_t s);
 cudaError_t launch_ranges(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_tiles,
                           cudaStream_t s);
+cudaError_t launch_tile_order(const ViewTable& vt, const Bufs& b, cudaStream_t s);
 cudaError_t launch_blend_fwd(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
                              cudaStream_t s);
 cudaError_t launch_point_scan(const ViewTable& vt, const Bufs& b, cudaStream_t s);

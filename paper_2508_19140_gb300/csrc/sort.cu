@@ -259,7 +259,8 @@ size_t scatter_smem() {
 template <int BITS>
 cudaError_t sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                       int64_t n, const uint32_t* d_n, int64_t cap, int shift, uint32_t* hist,
-                      int64_t hist_tiles, uint32_t* bin_total, cudaStream_t s) {
+                      int64_t hist_tiles, uint32_t* bin_total, cudaStream_t s,
+                      const char* const names[3]) {
     static bool attr_set = false;
     const size_t smem = scatter_smem<BITS>();
     if (!attr_set) {
@@ -273,10 +274,19 @@ cudaError_t sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, 
     const int sms = num_sms();
     const unsigned gh = (unsigned)(tiles_cap < (int64_t)sms * 8 ? tiles_cap : (int64_t)sms * 8);
     const unsigned gs = (unsigned)(tiles_cap < (int64_t)sms * 4 ? tiles_cap : (int64_t)sms * 4);
-    k_radix_hist<BITS><<<gh, kThreads, 0, s>>>(kin, n, d_n, shift, hist, hist_tiles, bin_total);
-    k_radix_scan<<<1 << BITS, 1024, 0, s>>>(hist, hist_tiles, bin_total, n, d_n);
-    k_radix_scatter<BITS><<<gs, kThreads, smem, s>>>(kin, vin, kout, vout, n, d_n, shift, hist,
-                                                      hist_tiles);
+    {
+        ProfScope ps(names[0], s);
+        k_radix_hist<BITS><<<gh, kThreads, 0, s>>>(kin, n, d_n, shift, hist, hist_tiles, bin_total);
+    }
+    {
+        ProfScope ps(names[1], s);
+        k_radix_scan<<<1 << BITS, 1024, 0, s>>>(hist, hist_tiles, bin_total, n, d_n);
+    }
+    {
+        ProfScope ps(names[2], s);
+        k_radix_scatter<BITS><<<gs, kThreads, smem, s>>>(kin, vin, kout, vout, n, d_n, shift, hist,
+                                                          hist_tiles);
+    }
     return cudaGetLastError();
 }
 
@@ -305,7 +315,8 @@ int64_t sort_hist_tiles(int64_t cap) { return (cap + kSortTile - 1) / kSortTile;
 
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n,
                        int64_t cap, const SortPlan& plan, uint32_t* hist, int64_t hist_tiles,
-                       uint32_t* bin_total, cudaStream_t s, int* result_buf) {
+                       uint32_t* bin_total, cudaStream_t s, int* result_buf,
+                       const char* const names[3]) {
     int cur = 0;
     *result_buf = 0;
     if (plan.passes == 0 || cap == 0) return cudaSuccess;
@@ -318,7 +329,7 @@ cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const ui
 #define RAST_PASS(B)                                                                              \
     case B:                                                                                       \
         e = sort_pass<B>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, d_n, cap,         \
-                         plan.shift[k], hist, hist_tiles, bt, s);                                 \
+                         plan.shift[k], hist, hist_tiles, bt, s, names);                          \
         break;
             RAST_PASS(4)
             RAST_PASS(5)

@@ -74,7 +74,8 @@ class View(ct.Structure):
 class Stats(ct.Structure):
     _fields_ = [("status", ct.c_int32), ("n_views", ct.c_int32), ("n_points", ct.c_int64),
                 ("n_copies", ct.c_int64), ("copy_capacity", ct.c_int64),
-                ("needed_records", ct.c_int64), ("n_tiles", ct.c_int64), ("n_pixels", ct.c_int64)]
+                ("needed_records", ct.c_int64), ("n_tiles", ct.c_int64), ("n_pixels", ct.c_int64),
+                ("needed_records_bwd", ct.c_int64)]
 
 
 class ProfileEntry(ct.Structure):
