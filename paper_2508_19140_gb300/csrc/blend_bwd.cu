@@ -171,8 +171,9 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
                     const float wgt = bilin_weight(px, py, i0, j0, s_a[r], s_b[r]);
                     const float ow = __fmul_rn(s_o[r], wgt);
                     const float alpha = fminf(ow, amax);
-                    const float inv = __frcp_rn(__fsub_rn(1.f, alpha));
-                    const float Tk = T * inv;
+                    const float om = __fsub_rn(1.f, alpha);
+                    const float Tk = __fdiv_rn(T, om);  // recursive: one rounding per step
+                    const float inv = __frcp_rn(om);
                     float fdot = 0.f;
 #pragma unroll
                     for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], s_f[c][r], fdot);
@@ -361,8 +362,9 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
                         const float o = s_o[r];
                         const float og = __fmul_rn(o, G);
                         const float alpha = fminf(og, amax);
-                        const float inv = __frcp_rn(__fsub_rn(1.f, alpha));
-                        const float Tk = T * inv;
+                        const float om = __fsub_rn(1.f, alpha);
+                        const float Tk = __fdiv_rn(T, om);  // recursive: one rounding per step
+                        const float inv = __frcp_rn(om);
                         float fdot = 0.f;
 #pragma unroll
                         for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], s_f[c][r], fdot);
