@@ -77,14 +77,16 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
         if (V.g_alpha) gA = V.g_alpha[pix];
         if (V.g_depth) gD = V.g_depth[pix];
     }
+    // Each thread clears its own mask row; the barriers inside block_max_u32
+    // order these stores before any thread sets bits in another pixel's row.
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
     const uint32_t maxlast = block_max_u32(last, &s_red);
     if (tid == 0 && maxlast) atomicAdd(&hdr->needed_bwd, (unsigned long long)maxlast);
     if (maxlast == 0) {
         if (tid == 0) cutoff[tile] = make_uint2(0u, 0u);
         return;
     }
-#pragma unroll
-    for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
     float Sg = 0.f, SD = 0.f;
     const float Kd = -gA * Tfin;  // constant part of the 1/(1-a) term
     const uint32_t end = rg.x + maxlast;
