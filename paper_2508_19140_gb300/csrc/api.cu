@@ -37,13 +37,13 @@ int bit_length(uint64_t x) {
 
 enum Slot {
     S_HDR, S_REC, S_RECT, S_CNT, S_ZBITS, S_KEYA0, S_KEYA1, S_VALA0, S_VALA1, S_RECTS, S_BASE, S_BLK,
-    S_KEYC0, S_KEYC1, S_VALC0, S_VALC1, S_PARTIAL, S_HIST, S_BINTOT, S_RANGES, S_ORDER, S_CUTOFF,
+    S_KEYC0, S_KEYC1, S_VALC0, S_VALC1, S_PARTIAL, S_HIST, S_BINTOT, S_RANGES, S_ORDER, S_CUTOFF, S_TRACE,
     S_TFINAL, S_LAST, S_COUNT
 };
 const char* kSlotNames[S_COUNT] = {
     "header", "records", "rect", "count", "zbits", "keys_a0", "keys_a1", "vals_a0", "vals_a1",
     "rect_sorted", "base", "block_sums", "keys_c0", "keys_c1", "vals_c0", "vals_c1",
-    "partial", "hist", "bin_total", "ranges", "tile_order", "cutoff", "t_final", "last"};
+    "partial", "hist", "bin_total", "ranges", "tile_order", "cutoff", "tile_trace", "t_final", "last"};
 
 struct Plan {
     ViewTable vt;
@@ -96,8 +96,10 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     vt.alpha_max = o->alpha_max;
     vt.dilation = o->dilation;
     vt.feat_word = o->mode == RAST_SPLAT_GAUSSIAN ? 8 : 4;
+    // Power-of-two record stride of at least 8 words (see RecLayout).
     const int fwords = vt.bf16 ? (C + 1) / 2 : C;
-    vt.rec_words = (vt.feat_word + fwords + 3) / 4 * 4;
+    const int need = vt.feat_word + fwords;
+    vt.rec_words = need <= 8 ? 8 : (need <= 16 ? 16 : 32);
     int64_t npt = 0, ntile = 0, npix = 0;
     uint32_t max_cull = 1;
     for (int k = 0; k < n_views; ++k) {
@@ -173,6 +175,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     pl.bytes[S_RANGES] = (size_t)ntile * 8;
     pl.bytes[S_ORDER] = (size_t)ntile * 4;
     pl.bytes[S_CUTOFF] = (size_t)ntile * 8;
+    pl.bytes[S_TRACE] = (size_t)ntile * 2 * 4 * 8;
     pl.bytes[S_TFINAL] = (size_t)npix * 4;
     pl.bytes[S_LAST] = (size_t)npix * 4;
     size_t off = 0;
@@ -183,6 +186,42 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     pl.total = off;
     return RAST_OK;
 }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+cudaError_t make_record_map(const ViewTable& vt, Bufs& b) {
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)vt.rec_words, (cuuint64_t)(vt.n_total > 0 ? vt.n_total : 1)};
+    const cuuint64_t strides[1] = {(cuuint64_t)vt.rec_words * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)vt.rec_words, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(&b.rec_map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, b.rec, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+namespace {
 
 Bufs make_bufs(const Plan& pl, void* ws) {
     char* w = static_cast<char*>(ws);
@@ -211,6 +250,7 @@ Bufs make_bufs(const Plan& pl, void* ws) {
     b.ranges = (uint2*)at(S_RANGES);
     b.order = (uint32_t*)at(S_ORDER);
     b.cutoff = (uint2*)at(S_CUTOFF);
+    b.trace = (unsigned long long*)at(S_TRACE);
     b.t_final = (float*)at(S_TFINAL);
     b.last = (uint32_t*)at(S_LAST);
     b.copy_cap = pl.copy_cap;
@@ -402,7 +442,8 @@ rast_status_t rasterize_batch(const rast_view_t* views, int32_t n_views, int32_t
     if (st != RAST_OK) return st;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return RAST_ERR_ARG;
     if (ws_bytes < pl.total) return RAST_ERR_CAPACITY;
-    const Bufs b = make_bufs(pl, workspace);
+    Bufs b = make_bufs(pl, workspace);
+    if (make_record_map(pl.vt, b) != cudaSuccess) return RAST_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (pass & RAST_PASS_FWD) {
         if (run_fwd(pl, b, s) != cudaSuccess) return RAST_ERR_CUDA;

@@ -37,19 +37,33 @@ __device__ __forceinline__ uint32_t block_max_u32(uint32_t x, uint32_t* s) {
 
 // ---------------------------------------------------------------- bilinear
 
+constexpr int kStages = 4;  // cp.async ring depth (batches in flight per CTA)
+
+template <int C, bool BF16>
+constexpr size_t bilinear_bwd_smem() {
+    return sizeof(uint32_t) * kStages * kBatch * RecLayout<0, C, BF16>::words  // record ring
+           + sizeof(uint32_t) * kStages * kBatch                              // slot-base ring
+           + sizeof(float) * 4 * (C + 1) * kBatch                             // contributions
+           + 128;
+}
+
 template <int C, bool BF16>
 __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec,
     const float* __restrict__ t_final, const uint32_t* __restrict__ last_in,
     const uint32_t* __restrict__ base, float* __restrict__ partial, uint2* __restrict__ cutoff,
-    WsHeader* __restrict__ hdr) {
+    WsHeader* __restrict__ hdr, unsigned long long* __restrict__ trace) {
+    const unsigned long long t_start = global_ns();
+    const long long c_start = clock64();
     constexpr int P = C + 1;  // dfeat[C], dopacity
-    __shared__ float s_a[kBatch], s_b[kBatch], s_o[kBatch], s_z[kBatch];
-    __shared__ int s_i0[kBatch], s_j0[kBatch];
-    __shared__ float s_f[C][kBatch];
+    constexpr int RW = RecLayout<0, C, BF16>::words;
+    constexpr int FW = RecLayout<0, C, BF16>::feat_word;
+    extern __shared__ __align__(128) uint32_t s_dyn[];
+    uint32_t* const s_ring = align128(s_dyn);                       // [kStages][kBatch][RW]
+    uint32_t* const s_base = s_ring + kStages * kBatch * RW;        // [kStages][kBatch]
+    float* const s_contrib = reinterpret_cast<float*>(s_base + kStages * kBatch);  // [4][P][kBatch]
     __shared__ uint32_t s_mask[kTilePix][9];
-    extern __shared__ float s_contrib[];  // [4 slots][P][kBatch]
     __shared__ uint32_t s_red;
 
     const int64_t tile = order[blockIdx.x];
@@ -60,7 +74,6 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
     const bool inside = px < V.W && py < V.H;
     const uint2 rg = ranges[tile];
-    const int RW = vt.rec_words, FW = vt.feat_word;
     const float amax = vt.alpha_max;
 
     float T = 1.f, Tfin = 1.f, gA = 0.f, gD = 0.f;
@@ -84,49 +97,60 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     const uint32_t maxlast = block_max_u32(last, &s_red);
     if (tid == 0 && maxlast) atomicAdd(&hdr->needed_bwd, (unsigned long long)maxlast);
     if (maxlast == 0) {
-        if (tid == 0) cutoff[tile] = make_uint2(0u, 0u);
+        if (tid == 0) {
+            cutoff[tile] = make_uint2(0u, 0u);
+            trace_tile(trace, tile, 1, t_start, c_start);
+        }
         return;
     }
     float Sg = 0.f, SD = 0.f;
     const float Kd = -gA * Tfin;  // constant part of the 1/(1-a) term
     const uint32_t end = rg.x + maxlast;
-    const int nb = (int)((maxlast - 1) / kBatch);
+    const uint32_t nb = (maxlast - 1) / kBatch + 1;  // batches, processed last to first
 
-    // Prologue: records (+ slot base) of the last batch, indices of the one before.
-    uint4 g = make_uint4(0u, 0u, 0u, 0u);
-    float f[C];
-    uint32_t gi = 0, bs = 0;
-    {
-        const uint32_t q = rg.x + (uint32_t)nb * kBatch + tid;
-        if (q < end) {
-            gi = pts[q];
-            const uint32_t* rp = rec + (size_t)gi * RW;
-            g = *reinterpret_cast<const uint4*>(rp);
-            load_features<C, BF16>(rp + FW, f);
-            bs = base[gi];
+    // Iteration j handles batch nb-1-j. Thread t copies record t of each batch
+    // (and its slot base); idx[k] = point of iteration j + kStages + k.
+    auto point_of = [&](uint32_t j) -> uint32_t {
+        if (j >= nb) return 0xffffffffu;
+        const uint32_t q = rg.x + (nb - 1 - j) * kBatch + tid;
+        return q < end ? pts[q] : 0xffffffffu;
+    };
+    auto issue = [&](uint32_t j, uint32_t gi) {
+        if (gi != 0xffffffffu) {
+            const int st = (int)(j % kStages);
+            uint32_t* dst = s_ring + ((size_t)st * kBatch + tid) * RW;
+            const uint32_t* src = rec + (size_t)gi * RW;
+#pragma unroll
+            for (int k = 0; k < RW; k += 4) cp_async16(dst + k, src + k);
+            cp_async4(s_base + st * kBatch + tid, base + gi);
         }
+        cp_async_commit();
+    };
+    uint32_t idx[kStages];
+    uint32_t gi_cur[kStages];  // point index per ring slot (for the cutoff record)
+#pragma unroll
+    for (int k = 0; k < kStages; ++k) idx[k] = point_of(k);
+#pragma unroll
+    for (int k = 0; k < kStages; ++k) {
+        issue(k, idx[k]);
+        gi_cur[k] = idx[k];
+        idx[k] = point_of(k + kStages);
     }
-    uint32_t gi_next = (nb > 0) ? pts[rg.x + (uint32_t)(nb - 1) * kBatch + tid] : 0u;
 
-    for (int bi = nb; bi >= 0; --bi) {
-        const uint32_t rel0 = (uint32_t)bi * kBatch;
-        const uint32_t b0 = rg.x + rel0;
-        const uint32_t q = b0 + tid;
+    for (uint32_t j = 0; j < nb; ++j) {
+        const uint32_t bi = nb - 1 - j;
+        const int st = (int)(j % kStages);
+        const uint32_t* ring = s_ring + (size_t)st * kBatch * RW;
+        const uint32_t rel0 = bi * kBatch;
+        const uint32_t q = rg.x + rel0 + tid;
         const bool have = q < end;
 #pragma unroll
         for (int k = 0; k < 4 * P; ++k) s_contrib[k * kBatch + tid] = 0.f;
-        int slot_base = 0, slot_w = 1, rtx = 0, rty = 0;
-        uint32_t my_gi = gi, my_bs = bs;
+        cp_async_wait<kStages - 1>();
+        int slot_base = 0;
         if (have) {
+            const uint4 g = *reinterpret_cast<const uint4*>(ring + tid * RW);
             const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
-            s_a[tid] = bg.a;
-            s_b[tid] = bg.b;
-            s_o[tid] = __uint_as_float(g.w);
-            s_z[tid] = __uint_as_float(g.z);
-            s_i0[tid] = bg.i0;
-            s_j0[tid] = bg.j0;
-#pragma unroll
-            for (int c = 0; c < C; ++c) s_f[c][tid] = f[c];
             const int X0 = bg.i0 - tx * kTile, Y0 = bg.j0 - ty * kTile;
             const uint32_t bit = 1u << lane;
 #pragma unroll
@@ -142,24 +166,16 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
             // The point's tile rect (as the projection computed it) and this tile's rank in it.
             const int tx0 = max(bg.i0, 0) / kTile, tx1 = min(bg.i0 + 1, V.W - 1) / kTile;
             const int ty0 = max(bg.j0, 0) / kTile;
-            slot_w = tx1 - tx0 + 1;
-            rtx = tx - tx0;
-            rty = ty - ty0;
-            slot_base = rty * slot_w + rtx;
-            if (q + 1 == end) cutoff[tile] = make_uint2(g.z, gi);
+            slot_base = (ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0);
+            if (q + 1 == end) {
+                uint32_t gi_last = gi_cur[0];
+#pragma unroll
+                for (int k = 1; k < kStages; ++k)
+                    if (st == k) gi_last = gi_cur[k];
+                cutoff[tile] = make_uint2(g.z, gi_last);
+            }
         }
         __syncthreads();
-        // Prefetch the previous batch (records + slot bases) and the indices before it.
-        if (bi > 0) {
-            const uint32_t qp = b0 - kBatch + tid;
-            gi = gi_next;
-            const uint32_t* rp = rec + (size_t)gi * RW;
-            g = *reinterpret_cast<const uint4*>(rp);
-            load_features<C, BF16>(rp + FW, f);
-            bs = base[gi];
-            (void)qp;
-            gi_next = (bi > 1) ? pts[b0 - 2 * kBatch + tid] : 0u;
-        }
         if (inside && last > rel0) {
 #pragma unroll 1
             for (int w = 7; w >= 0; --w) {
@@ -169,23 +185,27 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
                     m &= ~(1u << bit);
                     const int r = w * 32 + bit;
                     if (rel0 + r >= last) continue;
-                    const int i0 = s_i0[r], j0 = s_j0[r];
-                    const float wgt = bilin_weight(px, py, i0, j0, s_a[r], s_b[r]);
-                    const float ow = __fmul_rn(s_o[r], wgt);
+                    const uint32_t* rp = ring + r * RW;
+                    const uint4 g = *reinterpret_cast<const uint4*>(rp);
+                    const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
+                    const float wgt = bilin_weight(px, py, bg.i0, bg.j0, bg.a, bg.b);
+                    const float ow = __fmul_rn(__uint_as_float(g.w), wgt);
                     const float alpha = fminf(ow, amax);
                     const float om = __fsub_rn(1.f, alpha);
                     const float Tk = __fdiv_rn(T, om);  // recursive: one rounding per step
                     const float inv = __frcp_rn(om);
+                    float f[C];
+                    load_features<C, BF16>(rp + FW, f);
                     float fdot = 0.f;
 #pragma unroll
-                    for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], s_f[c][r], fdot);
-                    const float z = s_z[r];
+                    for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], f[c], fdot);
+                    const float z = __uint_as_float(g.z);
                     const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) * inv;
                     const float ta = Tk * alpha;
                     Sg = fmaf(ta, fdot, Sg);
                     SD = fmaf(ta, z, SD);
                     T = Tk;
-                    const int slot = (px - i0) + 2 * (py - j0);
+                    const int slot = (px - bg.i0) + 2 * (py - bg.j0);
                     float* cb = s_contrib + (slot * P) * kBatch + r;
 #pragma unroll
                     for (int c = 0; c < C; ++c) cb[c * kBatch] = ta * gF[c];
@@ -197,17 +217,25 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
         for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
         __syncthreads();
         if (have) {
-            float* out = partial + (size_t)(my_bs + (uint32_t)slot_base) * P;
+            float* out = partial + (size_t)(s_base[st * kBatch + tid] + (uint32_t)slot_base) * P;
 #pragma unroll
             for (int k = 0; k < P; ++k) {
                 const float* cb = s_contrib + k * kBatch + tid;
                 out[k] = ((cb[0] + cb[P * kBatch]) + cb[2 * P * kBatch]) + cb[3 * P * kBatch];
             }
         }
-        (void)my_gi;
-        (void)rty;
         __syncthreads();
+        // Slot st is free: refill it with iteration j + kStages.
+        issue(j + kStages, idx[0]);
+#pragma unroll
+        for (int k = 0; k < kStages; ++k)
+            if (st == k) gi_cur[k] = idx[0];
+#pragma unroll
+        for (int k = 0; k + 1 < kStages; ++k) idx[k] = idx[k + 1];
+        idx[kStages - 1] = point_of(j + 2 * kStages);
     }
+    cp_async_wait<0>();
+    if (tid == 0) trace_tile(trace, tile, 1, t_start, c_start);
 }
 
 // ---------------------------------------------------------------- Gaussian
@@ -532,7 +560,7 @@ template <int C, bool BF16>
 cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     const unsigned grid = (unsigned)vt.tiles_total;
     if (vt.mode == 0) {
-        constexpr size_t smem = sizeof(float) * 4 * (C + 1) * kBatch;
+        constexpr size_t smem = bilinear_bwd_smem<C, BF16>();
         static bool set = false;
         if (!set) {
             cudaError_t e = cudaFuncSetAttribute(k_blend_bwd_bilinear<C, BF16>,
@@ -542,7 +570,8 @@ cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts
         }
         ProfScope ps("blend_bwd", s);
         k_blend_bwd_bilinear<C, BF16><<<grid, kBlendThreads, smem, s>>>(
-            vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.cutoff, b.hdr);
+            vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.cutoff, b.hdr,
+            b.trace);
     } else {
         constexpr size_t smem = sizeof(float) * 8 * (C + 7) * kGBatch;
         static bool set = false;

@@ -65,15 +65,25 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ r
     }
 }
 
+constexpr int kStages = 4;  // cp.async ring depth (batches in flight per CTA)
+
+template <int C, bool BF16>
+constexpr size_t bilinear_fwd_smem() {
+    return sizeof(uint32_t) * kStages * kBatch * RecLayout<0, C, BF16>::words + 128;
+}
+
 template <int C, bool BF16>
 __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec, float* __restrict__ t_final,
-    uint32_t* __restrict__ last_out, WsHeader* __restrict__ hdr) {
-    __shared__ float s_a[kBatch], s_b[kBatch], s_o[kBatch], s_z[kBatch];
-    __shared__ int s_i0[kBatch], s_j0[kBatch];
-    __shared__ float s_f[C][kBatch];
-    __shared__ uint32_t s_mask[kTilePix][9];  // 8 words + 1 pad: conflict-free row reads
+    uint32_t* __restrict__ last_out, WsHeader* __restrict__ hdr, unsigned long long* __restrict__ trace) {
+    const unsigned long long t_start = global_ns();
+    const long long c_start = clock64();
+    constexpr int RW = RecLayout<0, C, BF16>::words;
+    constexpr int FW = RecLayout<0, C, BF16>::feat_word;
+    extern __shared__ __align__(128) uint32_t s_dyn[];
+    uint32_t* const s_ring = align128(s_dyn);  // [kStages][kBatch][RW] raw records
+    __shared__ uint32_t s_mask[kTilePix][9];   // 8 words + 1 pad: conflict-free row reads
     __shared__ uint32_t s_maxstop;
 
     const int64_t tile = order[blockIdx.x];
@@ -84,7 +94,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
     const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
     const bool inside = px < V.W && py < V.H;
     const uint2 rg = ranges[tile];
-    const int RW = vt.rec_words, FW = vt.feat_word;
+    const uint32_t len = rg.y - rg.x;
+    const uint32_t nbatch = (len + kBatch - 1) / kBatch;
     const float amax = vt.alpha_max, tmin = vt.t_min;
 
     float T = 1.f, A = 0.f, Dp = 0.f;
@@ -97,31 +108,37 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
     for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
     if (tid == 0) s_maxstop = 0;
 
-    // Prologue: records of batch 0 and indices of batch 1 in flight.
-    uint4 g = make_uint4(0u, 0u, 0u, 0u);
-    float f[C];
-    {
-        const uint32_t q = rg.x + tid;
-        if (q < rg.y) {
-            const uint32_t* rp = rec + (size_t)pts[q] * RW;
-            g = *reinterpret_cast<const uint4*>(rp);
-            load_features<C, BF16>(rp + FW, f);
-        }
-    }
-    uint32_t gi_next = (rg.x + kBatch + tid < rg.y) ? pts[rg.x + kBatch + tid] : 0u;
-    __syncthreads();
-
-    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBatch) {
-        if (b0 + tid < rg.y) {
-            const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
-            s_a[tid] = bg.a;
-            s_b[tid] = bg.b;
-            s_o[tid] = __uint_as_float(g.w);
-            s_z[tid] = __uint_as_float(g.z);
-            s_i0[tid] = bg.i0;
-            s_j0[tid] = bg.j0;
+    // Thread t copies record t of every batch. idx[k] = point index of batch
+    // (j + kStages + k) while batch j is processed (loaded kStages batches ahead).
+    auto point_of = [&](uint32_t j) -> uint32_t {
+        const uint32_t r = j * kBatch + tid;
+        return r < len ? pts[rg.x + r] : 0xffffffffu;
+    };
+    auto issue = [&](uint32_t j, uint32_t gi) {
+        if (gi != 0xffffffffu) {
+            uint32_t* dst = s_ring + ((size_t)(j % kStages) * kBatch + tid) * RW;
+            const uint32_t* src = rec + (size_t)gi * RW;
 #pragma unroll
-            for (int c = 0; c < C; ++c) s_f[c][tid] = f[c];
+            for (int k = 0; k < RW; k += 4) cp_async16(dst + k, src + k);
+        }
+        cp_async_commit();
+    };
+    uint32_t idx[kStages];
+#pragma unroll
+    for (int k = 0; k < kStages; ++k) idx[k] = point_of(k);
+#pragma unroll
+    for (int k = 0; k < kStages; ++k) {
+        issue(k, idx[k]);
+        idx[k] = point_of(k + kStages);
+    }
+
+    for (uint32_t j = 0; j < nbatch; ++j) {
+        const uint32_t* ring = s_ring + (size_t)(j % kStages) * kBatch * RW;
+        cp_async_wait<kStages - 1>();  // this thread's copy of batch j has landed
+        const uint32_t rel0 = j * kBatch;
+        if (rel0 + tid < len) {
+            const uint2 uv = *reinterpret_cast<const uint2*>(ring + tid * RW);
+            const BilinGeom bg = bilin_geom(__uint_as_float(uv.x), __uint_as_float(uv.y));
             const int X0 = bg.i0 - tx * kTile, Y0 = bg.j0 - ty * kTile;
             const uint32_t bit = 1u << lane;
 #pragma unroll
@@ -136,36 +153,30 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
             }
         }
         if (__syncthreads_count(!done) == 0) break;
-        // Prefetch: records of the next batch, indices of the one after.
-        {
-            const uint32_t qn = b0 + kBatch + tid;
-            if (qn < rg.y) {
-                const uint32_t* rp = rec + (size_t)gi_next * RW;
-                g = *reinterpret_cast<const uint4*>(rp);
-                load_features<C, BF16>(rp + FW, f);
-            }
-            gi_next = (qn + kBatch < rg.y) ? pts[qn + kBatch] : 0u;
-        }
         if (!done) {
-            const uint32_t rel0 = b0 - rg.x;
 #pragma unroll 1
             for (int w = 0; w < 8 && !done; ++w) {
                 uint32_t m = s_mask[tid][w];
                 while (m) {
                     const int r = w * 32 + __ffs(m) - 1;
                     m &= m - 1;
-                    const float wgt = bilin_weight(px, py, s_i0[r], s_j0[r], s_a[r], s_b[r]);
-                    const float alpha = fminf(__fmul_rn(s_o[r], wgt), amax);
+                    const uint32_t* rp = ring + r * RW;
+                    const uint4 g = *reinterpret_cast<const uint4*>(rp);
+                    const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
+                    const float wgt = bilin_weight(px, py, bg.i0, bg.j0, bg.a, bg.b);
+                    const float alpha = fminf(__fmul_rn(__uint_as_float(g.w), wgt), amax);
                     const float nT = __fmul_rn(T, __fsub_rn(1.f, alpha));
                     if (nT < tmin) {
                         done = true;
                         stop = rel0 + r + 1;
                         break;
                     }
+                    float f[C];
+                    load_features<C, BF16>(rp + FW, f);
                     const float ta = T * alpha;
 #pragma unroll
-                    for (int c = 0; c < C; ++c) F[c] = fmaf(ta, s_f[c][r], F[c]);
-                    Dp = fmaf(ta, s_z[r], Dp);
+                    for (int c = 0; c < C; ++c) F[c] = fmaf(ta, f[c], F[c]);
+                    Dp = fmaf(ta, __uint_as_float(g.z), Dp);
                     A += ta;
                     T = nT;
                     last = rel0 + r + 1;
@@ -175,7 +186,13 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
 #pragma unroll
         for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
         __syncthreads();
+        // Slot j % kStages is free: refill it with batch j + kStages.
+        issue(j + kStages, idx[0]);
+#pragma unroll
+        for (int k = 0; k + 1 < kStages; ++k) idx[k] = idx[k + 1];
+        idx[kStages - 1] = point_of(j + 2 * kStages);
     }
+    cp_async_wait<0>();  // no copy may land after the CTA has exited
 
     if (inside) {
         const int64_t pix = (int64_t)py * V.W + px;
@@ -196,8 +213,10 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
     const int open = __syncthreads_or(inside && stop == 0);
     if (stop) atomicMax(&s_maxstop, stop);
     __syncthreads();
-    if (tid == 0)
+    if (tid == 0) {
         atomicAdd(&hdr->needed, (unsigned long long)(open ? (rg.y - rg.x) : s_maxstop));
+        trace_tile(trace, tile, 0, t_start, c_start);
+    }
 }
 
 constexpr int kGroups = kBatch / 32;
@@ -342,10 +361,23 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
 template <int C, bool BF16>
 cudaError_t launch_fwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     const unsigned grid = (unsigned)vt.tiles_total;
+    if (vt.mode == 0) {
+        constexpr size_t smem = bilinear_fwd_smem<C, BF16>();
+        static bool set = false;
+        if (!set) {
+            cudaError_t e = cudaFuncSetAttribute(k_blend_fwd_bilinear<C, BF16>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            set = true;
+        }
+        ProfScope ps("blend_fwd", s);
+        k_blend_fwd_bilinear<C, BF16><<<grid, kBlendThreads, smem, s>>>(vt, b.ranges, b.order, pts, b.rec,
+                                                                        b.t_final, b.last, b.hdr, b.trace);
+        return cudaGetLastError();
+    }
     ProfScope ps("blend_fwd", s);
-    if (vt.mode == 0)
-        k_blend_fwd_bilinear<C, BF16><<<grid, kBlendThreads, 0, s>>>(vt, b.ranges, b.order, pts, b.rec,
-                                                                     b.t_final, b.last, b.hdr);
+    if (false)
+        ;
     else
         k_blend_fwd_gauss<C, BF16><<<grid, kBlendThreads, 0, s>>>(vt, b.ranges, b.order, pts, b.rec,
                                                                   b.t_final, b.last, b.hdr);

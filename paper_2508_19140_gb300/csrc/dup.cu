@@ -34,11 +34,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp
         uint32_t w = lane < NW ? s_warp[lane] : 0u;
         const uint32_t wi = warp_incl_scan(w);
         if (lane < NW) s_warp[lane] = wi - w;
-        if (lane == NW - 1) s_warp[31] = wi;
+        if (lane == NW - 1) s_warp[32] = wi;
     }
     __syncthreads();
     const uint32_t res = s_warp[warp] + inc - x;
-    total = s_warp[31];
+    total = s_warp[32];
     __syncthreads();
     return res;
 }
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kT) k_dup_count(const uint32_t* __restrict__ s
                                                   const uint2* __restrict__ rect,
                                                   uint2* __restrict__ rectS, int64_t n,
                                                   uint32_t* __restrict__ blk) {
-    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_warp[33];
     const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
     uint32_t c = 0;
 #pragma unroll
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kT) k_dup_count(const uint32_t* __restrict__ s
 // Block sums of a per-point count array (point order).
 __global__ void __launch_bounds__(kT) k_count_blocks(const uint32_t* __restrict__ cnt, int64_t n,
                                                      uint32_t* __restrict__ blk) {
-    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_warp[33];
     const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
     uint32_t c = 0;
 #pragma unroll
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kT) k_count_blocks(const uint32_t* __restrict_
 // empty copy list instead of a truncated one.
 __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ blk, int64_t nb,
                                                       WsHeader* hdr, int64_t cap) {
-    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_warp[33];
     __shared__ unsigned long long s_wtot[32];
     const int64_t per = (nb + 1023) / 1024;
     const int64_t lo = threadIdx.x * per;
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kT) k_dup_write(const ViewTable vt, const uint
                                                   const uint32_t* __restrict__ blk,
                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                   int64_t cap) {
-    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_warp[33];
     const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
     uint32_t off = blk[blockIdx.x];
 #pragma unroll 1
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kT) k_dup_write(const ViewTable vt, const uint
 __global__ void __launch_bounds__(kT) k_scan_apply(const uint32_t* __restrict__ cnt, int64_t n,
                                                    const uint32_t* __restrict__ blk,
                                                    uint32_t* __restrict__ base) {
-    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_warp[33];
     const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
     uint32_t off = blk[blockIdx.x];
 #pragma unroll 1

@@ -2,6 +2,7 @@
 // Shared by the kernel translation units and the C-ABI layer in api.cu.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -97,6 +98,28 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t sm_id() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+// Per-tile trace record written by one thread of a blend CTA.
+__device__ __forceinline__ void trace_tile(unsigned long long* tr, int64_t tile, int pass,
+                                           unsigned long long t0, long long c0) {
+    unsigned long long* e = tr + (tile * 2 + pass) * 4;
+    e[0] = t0;
+    e[1] = global_ns();
+    e[2] = (unsigned long long)(clock64() - c0);
+    e[3] = sm_id();
+}
+
 __device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
@@ -143,9 +166,11 @@ struct Bufs {
     uint2* ranges;
     uint32_t* order;      // tiles, heaviest list first
     uint2* cutoff;        // backward: (depth bits, point) of the last record processed per tile
+    unsigned long long* trace;  // per tile x {fwd, bwd}: start ns, end ns, cycles, SM id
     float* t_final;
     uint32_t* last;
     WsHeader* hdr;
+    CUtensorMap rec_map;  // records as a [n_points][rec_words] u32 tensor, one-row boxes (TMA gather4)
     int64_t copy_cap;
     int64_t hist_tiles;
     int64_t blk_cap;
@@ -182,6 +207,9 @@ cudaError_t launch_blend_bwd(const ViewTable& vt, const Bufs& b, const uint32_t*
 cudaError_t launch_reduce_grads(const ViewTable& vt, const Bufs& b, cudaStream_t s);
 
 bool channels_supported(int C);
+
+// Encodes b.rec_map for the records array (host; needs the driver entry point).
+cudaError_t make_record_map(const ViewTable& vt, Bufs& b);
 
 constexpr int kScanItems = 1024;   // items per block in the dup / point scans
 

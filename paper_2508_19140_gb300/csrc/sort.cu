@@ -98,7 +98,9 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
 }
 
 // Exclusive scan across a block of NT threads (NT <= 1024); returns the
-// thread's exclusive prefix, `total` gets the block sum. Uses s_warp[32].
+// thread's exclusive prefix, `total` gets the block sum. Uses s_warp[33]:
+// [0, 32) the warps' exclusive prefixes, [32] the total (kept apart so a
+// 32-warp block does not overwrite warp 31's prefix with it).
 template <int NT>
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp, uint32_t& total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -110,11 +112,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp
         uint32_t w = lane < NW ? s_warp[lane] : 0u;
         const uint32_t wi = warp_incl_scan(w);
         if (lane < NW) s_warp[lane] = wi - w;
-        if (lane == NW - 1) s_warp[31] = wi;
+        if (lane == NW - 1) s_warp[32] = wi;
     }
     __syncthreads();
     const uint32_t res = s_warp[warp] + inc - x;
-    total = s_warp[31];
+    total = s_warp[32];
     __syncthreads();
     return res;
 }
@@ -122,7 +124,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp
 __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist, int64_t hist_tiles,
                                                      const uint32_t* __restrict__ bin_total,
                                                      int64_t n_host, const uint32_t* d_n) {
-    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_warp[33];
     const int bin = blockIdx.x;
     const int64_t n = read_count(n_host, d_n);
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
     uint32_t* s_whist = s_vals + kSortTile;        // 8 * BINS: per-warp counts, then prefixes
     uint32_t* s_excl = s_whist + 8 * BINS;         // BINS: tile-local digit starts
     uint32_t* s_gbase = s_excl + BINS;             // BINS: global digit starts of this tile
-    uint32_t* s_warp = s_gbase + BINS;             // 32
+    uint32_t* s_warp = s_gbase + BINS;             // 33
     const int64_t n = read_count(n_host, d_n);
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
 template <int BITS>
 size_t scatter_smem() {
     constexpr int BINS = 1 << BITS;
-    return sizeof(uint32_t) * (2 * kSortTile + 8 * BINS + 2 * BINS + 32);
+    return sizeof(uint32_t) * (2 * kSortTile + 8 * BINS + 2 * BINS + 33);
 }
 
 template <int BITS>

@@ -101,11 +101,11 @@ def test_workspace_size_and_layout(lib):
     assert lay["records"][1] == 1000 * 8 * 4  # bilinear, 4 f32 features: 32-byte records
     assert lay["ranges"][1] == 7 * 4 * 8      # ceil(100/16) x ceil(60/16) tiles
     assert lay["t_final"][1] == 100 * 60 * 4
-    # gaussian: 48-byte records, 16 copies per point by default
+    # gaussian: 64-byte records (power-of-two stride), 16 copies per point by default
     og = _opts(lib, mode=1)
     n = lib.rasterize_workspace_layout(arr, 1, ct.byref(og), ents, len(ents))
     lay = {e.name.decode(): (e.offset, e.bytes) for e in ents}
-    assert lay["records"][1] == 1000 * 12 * 4
+    assert lay["records"][1] == 1000 * 16 * 4
     assert lay["sorted_keys"][1] == 16 * 1000 * 4
 
 
