@@ -150,6 +150,26 @@ rast_status_t rasterize_fwd(const rast_points_t* pts, const rast_camera_t* cam,
                             const rast_opts_t* opts, void* workspace, size_t ws_bytes,
                             const rast_images_t* out, void* stream);
 
+/* Forward pass of ONE view like rasterize_fwd, but allocating nothing and
+ * taking no workspace: for callers that cannot allocate device memory where
+ * they render (a plug-in inside an application that owns all GPU
+ * allocations, or a path that must not allocate during stream capture). No
+ * counterpart in the paper: it is a deployment convenience.
+ * The intermediate arrays live in one static device array of 16 MiB
+ * (1 << 24 bytes) that every GPU loading the library keeps until exit;
+ * problems whose rasterize_workspace_size() exceeds it return
+ * RAST_ERR_CAPACITY before any device work (e.g. 65,536 points at 256x256
+ * with 4 f32 features fit). The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. Every call reuses the same array and
+ * finds the previous call's contents there (the forward clears what it needs
+ * zeroed); calls whose GPU work overlaps race on it and must be serialised by
+ * the caller. Writes out->feat, out->alpha, out->depth; no backward state is
+ * kept for the caller. */
+rast_status_t rasterize_fwd_noalloc(const rast_points_t* pts, const rast_camera_t* cam,
+                                   const rast_opts_t* opts, const rast_images_t* out,
+                                   void* stream);
+
 /* Backward pass of ONE view (appendix Eq. 2, corrected). `workspace` must
  * hold the state of the matching rasterize_fwd on the same inputs. Writes
  * every element of the d_* outputs given (zeros for culled points). */

@@ -92,6 +92,8 @@ SIGNATURES = {
     "rasterize_workspace_size": (ct.c_size_t, [ct.POINTER(View), ct.c_int32, ct.POINTER(Opts)]),
     "rasterize_fwd": (ct.c_int, [ct.POINTER(Points), ct.POINTER(Camera), ct.POINTER(Opts),
                                  ct.c_void_p, ct.c_size_t, ct.POINTER(Images), ct.c_void_p]),
+    "rasterize_fwd_noalloc": (ct.c_int, [ct.POINTER(Points), ct.POINTER(Camera), ct.POINTER(Opts),
+                                         ct.POINTER(Images), ct.c_void_p]),
     "rasterize_bwd": (ct.c_int, [ct.POINTER(Points), ct.POINTER(Camera), ct.POINTER(Opts),
                                  ct.c_void_p, ct.c_size_t, ct.POINTER(Grads), ct.c_void_p]),
     "rasterize_batch": (ct.c_int, [ct.POINTER(View), ct.c_int32, ct.c_int32, ct.POINTER(Opts),
@@ -237,6 +239,15 @@ def rasterize_fwd(points: Points, camera: Camera, opts: Opts, workspace, out: Im
     s = load_library().rasterize_fwd(ct.byref(points), ct.byref(camera), ct.byref(opts),
                                      _ptr(workspace), workspace.numel(), ct.byref(out), _stream(stream))
     _check(s, "rasterize_fwd")
+
+
+def rasterize_fwd_noalloc(points: Points, camera: Camera, opts: Opts, out: Images, stream=None):
+    """Forward of one view without a workspace or any device allocation (the
+    library's static 16 MiB scratch holds the intermediates); raises RastError
+    with RAST_ERR_CAPACITY when the problem does not fit."""
+    s = load_library().rasterize_fwd_noalloc(ct.byref(points), ct.byref(camera), ct.byref(opts),
+                                             ct.byref(out), _stream(stream))
+    _check(s, "rasterize_fwd_noalloc")
 
 
 def rasterize_bwd(points: Points, camera: Camera, opts: Opts, workspace, grads: Grads, stream=None):
