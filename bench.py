@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--graph", type=int, default=-1,
+                    help="time CUDA-graph replays of the step (default: on for the batched 8-view workload)")
     return ap.parse_args()
 
 
@@ -155,25 +157,13 @@ def kernel_bytes(name, w):
 
 # ----------------------------------------------------------------------------- our arm
 
-def run_ours(args, ws_, rank, local):
+def make_views(scene, dev, bf16):
+    """Device tensors and C-ABI view structs for every view of a scene."""
     import torch
 
-    from paper_2508_19140_gb300 import build as build_mod
-    from paper_2508_19140_gb300 import rast, scenes
+    from paper_2508_19140_gb300 import rast
 
-    build_mod.build()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    dist = None
-    if ws_ > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-
-    scene = scenes.make_scene(args.config, seed=1000 + args.config + 7919 * rank,
-                              scale_points=args.scale_points)
-    bf16 = scene.feat_dtype == "bf16"
     gauss = scene.mode == "gaussian"
-    opts = rast.make_opts(mode=scene.mode)
     tens, cviews = [], []
     for v in scene.views:
         t = {}
@@ -197,14 +187,75 @@ def run_ours(args, ws_, rank, local):
         cv.pts = rast.make_points(t["xyz"], t["op"], t["feat"], t["scale"])
         cv.cam = rast.make_camera(v.camera)
         cv.out = rast.make_images(t["F"], t["A"], t["D"])
-        cv.grad = rast.make_grads(t["gF"], t["gA"], t["gD"], t["d_feat"], t["d_op"], t["d_xyz"], t["d_scale"])
+        cv.grad = rast.make_grads(t["gF"], t["gA"], t["gD"], t["d_feat"], t["d_op"], t["d_xyz"],
+                                  t["d_scale"])
         tens.append(t)
         cviews.append(cv)
+    return tens, cviews
+
+
+def sequential_f32_ms(scene, dev, opts, reps, flush):
+    """The same views as separate single-view FP32 rasterize_fwd + rasterize_bwd
+    calls (no batching, no graph): the baseline the batched BF16 graph path is
+    compared with."""
+    import torch
+
+    from paper_2508_19140_gb300 import rast
+
+    tens, cviews = make_views(scene, dev, bf16=False)
+    nbytes = max(rast.rasterize_workspace_size([cv], opts) for cv in cviews)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def run():
+        for cv in cviews:
+            rast.rasterize_fwd(cv.pts, cv.cam, opts, ws, cv.out, stream)
+            if scene.backward:
+                rast.rasterize_bwd(cv.pts, cv.cam, opts, ws, cv.grad, stream)
+
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    del tens, ws
+    return tot / reps
+
+
+def run_ours(args, ws_, rank, local):
+    import torch
+
+    from paper_2508_19140_gb300 import build as build_mod
+    from paper_2508_19140_gb300 import rast, scenes
+
+    build_mod.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if ws_ > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    scene = scenes.make_scene(args.config, seed=1000 + args.config + 7919 * rank,
+                              scale_points=args.scale_points)
+    bf16 = scene.feat_dtype == "bf16"
+    gauss = scene.mode == "gaussian"
+    opts = rast.make_opts(mode=scene.mode)
+    tens, cviews = make_views(scene, dev, bf16)
     ws_bytes = rast.rasterize_workspace_size(cviews, opts)
     wsp = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     n_points = sum(v.xyz.shape[0] for v in scene.views)
     do_bwd = scene.backward
+    use_graph = (args.graph == 1) or (args.graph == -1 and len(scene.views) > 1)
 
     def step():
         rast.rasterize_batch(cviews, rast.PASS_FWD | (rast.PASS_BWD if do_bwd else 0), opts, wsp, stream)
@@ -213,6 +264,19 @@ def run_ours(args, ws_, rank, local):
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
+    graph = None
+    if use_graph:
+        # One replayable graph of the whole fwd+bwd step (no host sync inside).
+        graph = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(dev)
+        cap.wait_stream(stream)
+        with torch.cuda.graph(graph, stream=cap):
+            rast.rasterize_batch(cviews, rast.PASS_FWD | (rast.PASS_BWD if do_bwd else 0), opts, wsp,
+                                 torch.cuda.current_stream(dev))
+        stream.wait_stream(cap)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
     st, stats = rast.rasterize_get_status(wsp, stream)
     if st != rast.RAST_OK:
         raise RuntimeError(f"rasterizer status {st}: {stats}")
@@ -224,14 +288,17 @@ def run_ours(args, ws_, rank, local):
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    rast.rasterize_profile_enable(True)
+    rast.rasterize_profile_enable(graph is None)
     evs = []
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step()
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
@@ -246,6 +313,25 @@ def run_ours(args, ws_, rank, local):
         dist.barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
+
+    prof_src = "live CUDA events around each kernel in the timed region"
+    if graph is not None:
+        rast.rasterize_profile_enable(True)
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        prof = rast.rasterize_profile_read()
+        rast.rasterize_profile_enable(False)
+        prof_src = "CUDA events around each kernel in non-graph steps right after the graph-timed region"
+
+    seq = None
+    if len(scene.views) > 1 and bf16 and rank == 0:
+        seq_ms = sequential_f32_ms(scene, dev, opts, max(3, args.steps // 4), flush)
+        seq = {"sequential_f32_ms": round(seq_ms, 4),
+               "batched_bf16_graph_ms": round(total_ms / max(args.steps, 1), 4),
+               "speedup": round(seq_ms / (total_ms / max(args.steps, 1)), 3),
+               "what": "same views: one batched BF16 graph replay vs per-view FP32 rasterize_fwd+rasterize_bwd calls without a graph"}
 
     # Forward-only timing (reported beside the headline).
     fwd_ms = None
@@ -292,7 +378,8 @@ def run_ours(args, ws_, rank, local):
                     "frac": round(ach / peak, 4), "traffic": None,
                     "peak_source": f"{peak_src} (hbm_gbs)"}
     blend = kernels.get("blend_fwd")
-    gpu_launches = int(sum(x[0] for x in prof.values()))
+    prof_steps = args.steps if graph is None else max(3, args.steps // 2)
+    gpu_launches = int(round(sum(x[0] for x in prof.values()) / max(prof_steps, 1) * args.steps))
 
     e2e = None
     if not args.no_e2e:
@@ -314,7 +401,8 @@ def run_ours(args, ws_, rank, local):
         "roofline": roofline,
         "blend_fwd_roofline": ({"achieved": blend["gbs"], "peak": peak, "unit": "GB/s",
                                 "frac": round((blend["gbs"] or 0) / peak, 4)} if blend else None),
-        "kernels": kernels, "gpu_launches": gpu_launches,
+        "kernels": kernels, "kernel_timing": prof_src, "gpu_launches": gpu_launches,
+        "graph": graph is not None, "batched_vs_sequential": seq,
         "clocks": clocks, "e2e": e2e,
     }
     return out, dist

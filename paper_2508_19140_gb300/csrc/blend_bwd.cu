@@ -37,13 +37,14 @@ __device__ __forceinline__ uint32_t block_max_u32(uint32_t x, uint32_t* s) {
 
 // ---------------------------------------------------------------- bilinear
 
-constexpr int kStages = 4;  // cp.async ring depth (batches in flight per CTA)
+constexpr int kStages = 3;  // cp.async ring depth (batches in flight per CTA)
 
 template <int C, bool BF16>
 constexpr size_t bilinear_bwd_smem() {
     return sizeof(uint32_t) * kStages * kBatch * RecLayout<0, C, BF16>::words  // record ring
            + sizeof(uint32_t) * kStages * kBatch                              // slot-base ring
-           + sizeof(float) * 4 * (C + 1) * kBatch                             // contributions
+           + sizeof(float) * 4 * 2 * kBatch                                   // (T a, w dL/da) per slot
+           + sizeof(float) * kTilePix * C                                     // upstream dL/dF per pixel
            + 128;
 }
 
@@ -60,10 +61,15 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     constexpr int RW = RecLayout<0, C, BF16>::words;
     constexpr int FW = RecLayout<0, C, BF16>::feat_word;
     extern __shared__ __align__(128) uint32_t s_dyn[];
-    uint32_t* const s_ring = align128(s_dyn);                       // [kStages][kBatch][RW]
-    uint32_t* const s_base = s_ring + kStages * kBatch * RW;        // [kStages][kBatch]
-    float* const s_contrib = reinterpret_cast<float*>(s_base + kStages * kBatch);  // [4][P][kBatch]
+    uint32_t* const s_ring = align128(s_dyn);                        // [kStages][kBatch][RW]
+    uint32_t* const s_base = s_ring + kStages * kBatch * RW;         // [kStages][kBatch]
+    float* const s_ta = reinterpret_cast<float*>(s_base + kStages * kBatch);  // [4][kBatch]
+    float* const s_da = s_ta + 4 * kBatch;                           // [4][kBatch]
+    float* const s_gF = s_da + 4 * kBatch;                           // [kTilePix][C]
     __shared__ uint32_t s_mask[kTilePix][9];
+    __shared__ float s_w[4][kBatch];    // bilinear weight per slot
+    __shared__ float s_o[kBatch];       // opacity per record
+    __shared__ uint32_t s_anchor[kBatch];
     __shared__ uint32_t s_red;
 
     const int64_t tile = order[blockIdx.x];
@@ -71,7 +77,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
+    const int lx = tid & 15, ly = tid >> 4;
+    const int px = tx * kTile + lx, py = ty * kTile + ly;
     const bool inside = px < V.W && py < V.H;
     const uint2 rg = ranges[tile];
     const float amax = vt.alpha_max;
@@ -90,6 +97,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
         if (V.g_alpha) gA = V.g_alpha[pix];
         if (V.g_depth) gD = V.g_depth[pix];
     }
+#pragma unroll
+    for (int c = 0; c < C; ++c) s_gF[tid * C + c] = gF[c];
     // Each thread clears its own mask row; the barriers inside block_max_u32
     // order these stores before any thread sets bits in another pixel's row.
 #pragma unroll
@@ -145,13 +154,24 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
         const uint32_t q = rg.x + rel0 + tid;
         const bool have = q < end;
 #pragma unroll
-        for (int k = 0; k < 4 * P; ++k) s_contrib[k * kBatch + tid] = 0.f;
+        for (int k = 0; k < 4; ++k) {
+            s_ta[k * kBatch + tid] = 0.f;
+            s_da[k * kBatch + tid] = 0.f;
+        }
         cp_async_wait<kStages - 1>();
-        int slot_base = 0;
+        int slot_base = 0, X0 = 0, Y0 = 0;
         if (have) {
             const uint4 g = *reinterpret_cast<const uint4*>(ring + tid * RW);
             const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
-            const int X0 = bg.i0 - tx * kTile, Y0 = bg.j0 - ty * kTile;
+            const float o = __uint_as_float(g.w);
+            const float ax = __fsub_rn(1.f, bg.a), by = __fsub_rn(1.f, bg.b);
+            const float w0 = __fmul_rn(ax, by), w1 = __fmul_rn(bg.a, by);
+            const float w2 = __fmul_rn(ax, bg.b), w3 = __fmul_rn(bg.a, bg.b);
+            s_w[0][tid] = w0; s_w[1][tid] = w1; s_w[2][tid] = w2; s_w[3][tid] = w3;
+            s_o[tid] = o;
+            X0 = bg.i0 - tx * kTile;
+            Y0 = bg.j0 - ty * kTile;
+            s_anchor[tid] = (uint32_t)(X0 + 1) | ((uint32_t)(Y0 + 1) << 8);
             const uint32_t bit = 1u << lane;
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
@@ -177,52 +197,63 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
         }
         __syncthreads();
         if (inside && last > rel0) {
+            // One loop over the set bits of the pixel's mask, last to first.
+            int w = 7;
+            uint32_t m = s_mask[tid][7];
 #pragma unroll 1
-            for (int w = 7; w >= 0; --w) {
-                uint32_t m = s_mask[tid][w];
-                while (m) {
-                    const int bit = 31 - __clz(m);
-                    m &= ~(1u << bit);
-                    const int r = w * 32 + bit;
-                    if (rel0 + r >= last) continue;
-                    const uint32_t* rp = ring + r * RW;
-                    const uint4 g = *reinterpret_cast<const uint4*>(rp);
-                    const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
-                    const float wgt = bilin_weight(px, py, bg.i0, bg.j0, bg.a, bg.b);
-                    const float ow = __fmul_rn(__uint_as_float(g.w), wgt);
-                    const float alpha = fminf(ow, amax);
-                    const float om = __fsub_rn(1.f, alpha);
-                    const float Tk = __fdiv_rn(T, om);  // recursive: one rounding per step
-                    const float inv = __frcp_rn(om);
-                    float f[C];
-                    load_features<C, BF16>(rp + FW, f);
-                    float fdot = 0.f;
+            while (true) {
+                while (m == 0 && w > 0) m = s_mask[tid][--w];
+                if (m == 0) break;
+                const int bit = 31 - __clz(m);
+                m &= ~(1u << bit);
+                const int r = w * 32 + bit;
+                if (rel0 + r >= last) continue;
+                const uint32_t an = s_anchor[r];
+                const int slot = (lx + 1 - (int)(an & 0xffu)) + 2 * (ly + 1 - (int)(an >> 8));
+                const float wgt = s_w[slot][r];
+                const float ow = __fmul_rn(s_o[r], wgt);
+                const float alpha = fminf(ow, amax);
+                const float om = __fsub_rn(1.f, alpha);
+                const float Tk = __fdiv_rn(T, om);  // recursive: one rounding per step
+                const float inv = __frcp_rn(om);
+                const uint32_t* rp = ring + r * RW;
+                float f[C];
+                load_features<C, BF16>(rp + FW, f);
+                float fdot = 0.f;
 #pragma unroll
-                    for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], f[c], fdot);
-                    const float z = __uint_as_float(g.z);
-                    const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) * inv;
-                    const float ta = Tk * alpha;
-                    Sg = fmaf(ta, fdot, Sg);
-                    SD = fmaf(ta, z, SD);
-                    T = Tk;
-                    const int slot = (px - bg.i0) + 2 * (py - bg.j0);
-                    float* cb = s_contrib + (slot * P) * kBatch + r;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) cb[c * kBatch] = ta * gF[c];
-                    cb[C * kBatch] = (ow <= amax) ? wgt * dalpha : 0.f;
-                }
+                for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], f[c], fdot);
+                const float z = __uint_as_float(rp[2]);
+                const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) * inv;
+                const float ta = Tk * alpha;
+                Sg = fmaf(ta, fdot, Sg);
+                SD = fmaf(ta, z, SD);
+                T = Tk;
+                s_ta[slot * kBatch + r] = ta;
+                s_da[slot * kBatch + r] = (ow <= amax) ? wgt * dalpha : 0.f;
             }
         }
 #pragma unroll
         for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
         __syncthreads();
         if (have) {
+            // dL/df = sum over the 2x2 slots (fixed order) of T a times the pixel's dL/dF.
+            float acc[P];
+#pragma unroll
+            for (int k = 0; k < P; ++k) acc[k] = 0.f;
+#pragma unroll
+            for (int sl = 0; sl < 4; ++sl) {
+                const int X = X0 + (sl & 1), Y = Y0 + (sl >> 1);
+                const float ta = s_ta[sl * kBatch + tid];
+                if ((unsigned)X < (unsigned)kTile && (unsigned)Y < (unsigned)kTile) {
+                    const float* gp = s_gF + (Y * kTile + X) * C;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) acc[c] += ta * gp[c];
+                }
+                acc[C] += s_da[sl * kBatch + tid];
+            }
             float* out = partial + (size_t)(s_base[st * kBatch + tid] + (uint32_t)slot_base) * P;
 #pragma unroll
-            for (int k = 0; k < P; ++k) {
-                const float* cb = s_contrib + k * kBatch + tid;
-                out[k] = ((cb[0] + cb[P * kBatch]) + cb[2 * P * kBatch]) + cb[3 * P * kBatch];
-            }
+            for (int k = 0; k < P; ++k) out[k] = acc[k];
         }
         __syncthreads();
         // Slot st is free: refill it with iteration j + kStages.

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ r
     }
 }
 
-constexpr int kStages = 4;  // cp.async ring depth (batches in flight per CTA)
+constexpr int kStages = 3;  // cp.async ring depth (batches in flight per CTA)
 
 template <int C, bool BF16>
 constexpr size_t bilinear_fwd_smem() {
@@ -84,6 +84,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
     extern __shared__ __align__(128) uint32_t s_dyn[];
     uint32_t* const s_ring = align128(s_dyn);  // [kStages][kBatch][RW] raw records
     __shared__ uint32_t s_mask[kTilePix][9];   // 8 words + 1 pad: conflict-free row reads
+    __shared__ float s_alpha[4][kBatch];       // alpha of each record's 2x2 slots (FP32, pinned ops)
+    __shared__ uint32_t s_anchor[kBatch];      // tile-local anchor (X0 + 1) | (Y0 + 1) << 8
     __shared__ uint32_t s_maxstop;
 
     const int64_t tile = order[blockIdx.x];
@@ -91,7 +93,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
+    const int lx = tid & 15, ly = tid >> 4;
+    const int px = tx * kTile + lx, py = ty * kTile + ly;
     const bool inside = px < V.W && py < V.H;
     const uint2 rg = ranges[tile];
     const uint32_t len = rg.y - rg.x;
@@ -137,9 +140,19 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
         cp_async_wait<kStages - 1>();  // this thread's copy of batch j has landed
         const uint32_t rel0 = j * kBatch;
         if (rel0 + tid < len) {
-            const uint2 uv = *reinterpret_cast<const uint2*>(ring + tid * RW);
-            const BilinGeom bg = bilin_geom(__uint_as_float(uv.x), __uint_as_float(uv.y));
+            // Per record: the four fragment alphas of its 2x2 box (the ops of
+            // bilin_weight and the clamp, so every pixel sees the same FP32 bits)
+            // and one mask bit per covered pixel of this tile.
+            const uint4 g = *reinterpret_cast<const uint4*>(ring + tid * RW);
+            const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
+            const float o = __uint_as_float(g.w);
+            const float ax = __fsub_rn(1.f, bg.a), by = __fsub_rn(1.f, bg.b);
+            s_alpha[0][tid] = fminf(__fmul_rn(o, __fmul_rn(ax, by)), amax);
+            s_alpha[1][tid] = fminf(__fmul_rn(o, __fmul_rn(bg.a, by)), amax);
+            s_alpha[2][tid] = fminf(__fmul_rn(o, __fmul_rn(ax, bg.b)), amax);
+            s_alpha[3][tid] = fminf(__fmul_rn(o, __fmul_rn(bg.a, bg.b)), amax);
             const int X0 = bg.i0 - tx * kTile, Y0 = bg.j0 - ty * kTile;
+            s_anchor[tid] = (uint32_t)(X0 + 1) | ((uint32_t)(Y0 + 1) << 8);
             const uint32_t bit = 1u << lane;
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
@@ -154,33 +167,34 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
         }
         if (__syncthreads_count(!done) == 0) break;
         if (!done) {
+            // One loop over every set bit of the pixel's 256-bit mask, in order.
+            int w = 0;
+            uint32_t m = s_mask[tid][0];
 #pragma unroll 1
-            for (int w = 0; w < 8 && !done; ++w) {
-                uint32_t m = s_mask[tid][w];
-                while (m) {
-                    const int r = w * 32 + __ffs(m) - 1;
-                    m &= m - 1;
-                    const uint32_t* rp = ring + r * RW;
-                    const uint4 g = *reinterpret_cast<const uint4*>(rp);
-                    const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
-                    const float wgt = bilin_weight(px, py, bg.i0, bg.j0, bg.a, bg.b);
-                    const float alpha = fminf(__fmul_rn(__uint_as_float(g.w), wgt), amax);
-                    const float nT = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                    if (nT < tmin) {
-                        done = true;
-                        stop = rel0 + r + 1;
-                        break;
-                    }
-                    float f[C];
-                    load_features<C, BF16>(rp + FW, f);
-                    const float ta = T * alpha;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) F[c] = fmaf(ta, f[c], F[c]);
-                    Dp = fmaf(ta, __uint_as_float(g.z), Dp);
-                    A += ta;
-                    T = nT;
-                    last = rel0 + r + 1;
+            while (true) {
+                while (m == 0 && w < 7) m = s_mask[tid][++w];
+                if (m == 0) break;
+                const int r = w * 32 + __ffs(m) - 1;
+                m &= m - 1;
+                const uint32_t an = s_anchor[r];
+                const int slot = (lx + 1 - (int)(an & 0xffu)) + 2 * (ly + 1 - (int)(an >> 8));
+                const float alpha = s_alpha[slot][r];
+                const float nT = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                if (nT < tmin) {
+                    done = true;
+                    stop = rel0 + r + 1;
+                    break;
                 }
+                const uint32_t* rp = ring + r * RW;
+                float f[C];
+                load_features<C, BF16>(rp + FW, f);
+                const float ta = T * alpha;
+#pragma unroll
+                for (int c = 0; c < C; ++c) F[c] = fmaf(ta, f[c], F[c]);
+                Dp = fmaf(ta, __uint_as_float(rp[2]), Dp);
+                A += ta;
+                T = nT;
+                last = rel0 + r + 1;
             }
         }
 #pragma unroll
