@@ -188,8 +188,17 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
         for (int r = 0; r < kIPT; ++r) {
             const int64_t idx = wbase + r * 32 + lane;
             const bool ok = idx < n;
-            const uint32_t d = ok ? ((k[r] >> shift) & (BINS - 1)) : (uint32_t)BINS;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t d = ok ? ((k[r] >> shift) & (BINS - 1)) : 0u;
+            // Lanes holding the same digit: one ballot per digit bit (and one
+            // for validity) instead of a match instruction.
+            uint32_t peers = __ballot_sync(0xffffffffu, ok);
+            if (!ok) peers = ~peers;
+#pragma unroll
+            for (int bb = 0; bb < BITS; ++bb) {
+                const bool set = (d >> bb) & 1u;
+                const uint32_t m = __ballot_sync(0xffffffffu, set);
+                peers &= set ? m : ~m;
+            }
             uint32_t pre = 0;
             if (ok) pre = s_whist[warp * BINS + d];
             __syncwarp();
