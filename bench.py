@@ -132,9 +132,9 @@ def kernel_bytes(name, w):
     rec, fb, npart = w["rec_bytes"], w["feat_bytes"], w["partial_floats"]
     if name == "project":
         return N * (12 + 4 + C * fb) + N * (rec + 4 + 4 + 8 + 4)
-    if name.endswith(".hist"):
+    if name.endswith(".hist"):      # one read of the keys counts every pass's digits
         return 4 * (N if name.startswith("depth") else D)
-    if name.endswith(".scatter"):
+    if name.endswith(".sweep"):     # per pass: read key+value, write key+value
         return 16 * (N if name.startswith("depth") else D)
     if name == "dup.count":
         return N * (4 + 8 + 8)

@@ -37,20 +37,20 @@ int bit_length(uint64_t x) {
 
 enum Slot {
     S_HDR, S_REC, S_RECT, S_CNT, S_ZBITS, S_KEYA0, S_KEYA1, S_VALA0, S_VALA1, S_RECTS, S_BASE, S_BLK,
-    S_KEYC0, S_KEYC1, S_VALC0, S_VALC1, S_PARTIAL, S_HIST, S_BINTOT, S_RANGES, S_ORDER, S_CUTOFF, S_TRACE,
+    S_KEYC0, S_KEYC1, S_VALC0, S_VALC1, S_PARTIAL, S_SGHIST, S_SCOUNT, S_SSTATUS, S_RANGES, S_ORDER, S_CUTOFF, S_TRACE,
     S_TFINAL, S_LAST, S_COUNT
 };
 const char* kSlotNames[S_COUNT] = {
     "header", "records", "rect", "count", "zbits", "keys_a0", "keys_a1", "vals_a0", "vals_a1",
     "rect_sorted", "base", "block_sums", "keys_c0", "keys_c1", "vals_c0", "vals_c1",
-    "partial", "hist", "bin_total", "ranges", "tile_order", "cutoff", "tile_trace", "t_final", "last"};
+    "partial", "sort_hist", "sort_counters", "sort_status", "ranges", "tile_order", "cutoff", "tile_trace", "t_final", "last"};
 
 struct Plan {
     ViewTable vt;
     size_t off[S_COUNT];
     size_t bytes[S_COUNT];
     size_t total;
-    int64_t copy_cap, hist_tiles, blk_cap;
+    int64_t copy_cap, blk_cap;
     SortPlan planA, planC;
     int partial_floats;
 };
@@ -143,16 +143,17 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
         ntile += (int64_t)d.tiles_x * d.tiles_y;
         npix += (int64_t)c.width * c.height;
     }
-    if (npt >= ((int64_t)1 << 31) || ntile >= ((int64_t)1 << 31) || npix >= ((int64_t)1 << 40))
+    if (npt >= ((int64_t)1 << 30) || ntile >= ((int64_t)1 << 30) || npix >= ((int64_t)1 << 40))
         return RAST_ERR_ARG;
     vt.n_total = npt;
     vt.tiles_total = ntile;
     vt.pix_total = npix;
 
     const int64_t per_pt = o->max_copies > 0 ? o->max_copies : (o->mode == RAST_SPLAT_BILINEAR ? 4 : 16);
+    // Copy capacity: sort prefixes are 30-bit values, so at most 2^30 - 1 copies
+    // (beyond that the forward reports RAST_ERR_CAPACITY).
     pl.copy_cap = npt * per_pt;
-    if (pl.copy_cap >= ((int64_t)1 << 32)) pl.copy_cap = ((int64_t)1 << 32) - 1;
-    pl.hist_tiles = sort_hist_tiles(npt > pl.copy_cap ? npt : pl.copy_cap);
+    if (pl.copy_cap >= ((int64_t)1 << 30)) pl.copy_cap = ((int64_t)1 << 30) - 1;
     pl.blk_cap = (npt + kScanItems - 1) / kScanItems + 1;
     pl.planA = make_sort_plan(bit_length(max_cull));
     pl.planC = make_sort_plan(bit_length((uint64_t)(ntile > 0 ? ntile - 1 : 0)));
@@ -170,8 +171,12 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     pl.bytes[S_BLK] = (size_t)pl.blk_cap * 4;
     pl.bytes[S_KEYC0] = pl.bytes[S_KEYC1] = pl.bytes[S_VALC0] = pl.bytes[S_VALC1] = (size_t)D * 4;
     pl.bytes[S_PARTIAL] = (size_t)D * pl.partial_floats * 4;
-    pl.bytes[S_HIST] = (size_t)512 * pl.hist_tiles * 4;
-    pl.bytes[S_BINTOT] = (size_t)512 * 8 * 4;
+    pl.bytes[S_SGHIST] = (size_t)4 * 512 * 4;
+    pl.bytes[S_SCOUNT] = (size_t)4 * 4;
+    {
+        const int64_t wa = sort_status_words(pl.planA, npt), wc = sort_status_words(pl.planC, pl.copy_cap);
+        pl.bytes[S_SSTATUS] = (size_t)(wa > wc ? wa : wc) * 4;
+    }
     pl.bytes[S_RANGES] = (size_t)ntile * 8;
     pl.bytes[S_ORDER] = (size_t)ntile * 4;
     pl.bytes[S_CUTOFF] = (size_t)ntile * 8;
@@ -245,8 +250,9 @@ Bufs make_bufs(const Plan& pl, void* ws) {
     b.valC[0] = (uint32_t*)at(S_VALC0);
     b.valC[1] = (uint32_t*)at(S_VALC1);
     b.partial = (float*)at(S_PARTIAL);
-    b.hist = (uint32_t*)at(S_HIST);
-    b.bin_total = (uint32_t*)at(S_BINTOT);
+    b.sort_ghist = (uint32_t*)at(S_SGHIST);
+    b.sort_counters = (uint32_t*)at(S_SCOUNT);
+    b.sort_status = (uint32_t*)at(S_SSTATUS);
     b.ranges = (uint2*)at(S_RANGES);
     b.order = (uint32_t*)at(S_ORDER);
     b.cutoff = (uint2*)at(S_CUTOFF);
@@ -254,7 +260,6 @@ Bufs make_bufs(const Plan& pl, void* ws) {
     b.t_final = (float*)at(S_TFINAL);
     b.last = (uint32_t*)at(S_LAST);
     b.copy_cap = pl.copy_cap;
-    b.hist_tiles = pl.hist_tiles;
     b.blk_cap = pl.blk_cap;
     return b;
 }
@@ -324,8 +329,8 @@ namespace {
         if (e_ != cudaSuccess) return e_;   \
     } while (0)
 
-const char* const kDepthSortNames[3] = {"depth_sort.hist", "depth_sort.scan", "depth_sort.scatter"};
-const char* const kTileSortNames[3] = {"tile_sort.hist", "tile_sort.scan", "tile_sort.scatter"};
+const char* const kDepthSortNames[2] = {"depth_sort.hist", "depth_sort.sweep"};
+const char* const kTileSortNames[2] = {"tile_sort.hist", "tile_sort.sweep"};
 
 cudaError_t run_fwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
     const ViewTable& vt = pl.vt;
@@ -340,16 +345,16 @@ cudaError_t run_fwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
     {
         uint32_t* k[2] = {b.keyA[0], b.keyA[1]};
         uint32_t* v[2] = {b.valA[0], b.valA[1]};
-        RAST_TRY(radix_sort(k, v, vt.n_total, nullptr, vt.n_total, pl.planA, b.hist, b.hist_tiles,
-                            b.bin_total, s, &ra, kDepthSortNames));
+        const SortScratch sc{b.sort_ghist, b.sort_counters, b.sort_status, &b.hdr->error};
+        RAST_TRY(radix_sort(k, v, vt.n_total, nullptr, vt.n_total, pl.planA, sc, s, &ra, kDepthSortNames));
     }
     const uint32_t* depth_sorted = b.valA[ra];
     RAST_TRY(launch_duplicate(vt, b, depth_sorted, s));
     {
         uint32_t* k[2] = {b.keyC[0], b.keyC[1]};
         uint32_t* v[2] = {b.valC[0], b.valC[1]};
-        RAST_TRY(radix_sort(k, v, 0, &b.hdr->n_copies, pl.copy_cap, pl.planC, b.hist, b.hist_tiles,
-                            b.bin_total, s, &rc, kTileSortNames));
+        const SortScratch sc{b.sort_ghist, b.sort_counters, b.sort_status, &b.hdr->error};
+        RAST_TRY(radix_sort(k, v, 0, &b.hdr->n_copies, pl.copy_cap, pl.planC, sc, s, &rc, kTileSortNames));
     }
     RAST_TRY(launch_ranges(vt, b, b.keyC[rc], s));
     RAST_TRY(launch_tile_order(vt, b, s));

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     float* const s_gF = s_da + 4 * kBatch;                           // [kTilePix][C]
     __shared__ uint32_t s_mask[kTilePix][9];
     __shared__ float s_w[4][kBatch];    // bilinear weight per slot
+    __shared__ float s_inv[4][kBatch];  // 1 / (1 - alpha) per slot
     __shared__ float s_o[kBatch];       // opacity per record
     __shared__ uint32_t s_anchor[kBatch];
     __shared__ uint32_t s_red;
@@ -169,6 +170,11 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
             const float w2 = __fmul_rn(ax, bg.b), w3 = __fmul_rn(bg.a, bg.b);
             s_w[0][tid] = w0; s_w[1][tid] = w1; s_w[2][tid] = w2; s_w[3][tid] = w3;
             s_o[tid] = o;
+            // 1 / (1 - alpha) of each slot, alpha = min(o w, amax) exactly as the forward has it
+            s_inv[0][tid] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w0), amax)));
+            s_inv[1][tid] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w1), amax)));
+            s_inv[2][tid] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w2), amax)));
+            s_inv[3][tid] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w3), amax)));
             X0 = bg.i0 - tx * kTile;
             Y0 = bg.j0 - ty * kTile;
             s_anchor[tid] = (uint32_t)(X0 + 1) | ((uint32_t)(Y0 + 1) << 8);
@@ -213,9 +219,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
                 const float wgt = s_w[slot][r];
                 const float ow = __fmul_rn(s_o[r], wgt);
                 const float alpha = fminf(ow, amax);
-                const float om = __fsub_rn(1.f, alpha);
-                const float Tk = __fdiv_rn(T, om);  // recursive: one rounding per step
-                const float inv = __frcp_rn(om);
+                const float inv = s_inv[slot][r];
+                const float Tk = T * inv;  // T_k = T_{k+1} / (1 - alpha_k)
                 const uint32_t* rp = ring + r * RW;
                 float f[C];
                 load_features<C, BF16>(rp + FW, f);
@@ -234,7 +239,16 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
         }
 #pragma unroll
         for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
+        const uint32_t my_base = s_base[st * kBatch + tid];  // read before the slot is refilled
         __syncthreads();
+        // Slot st is free (every pixel is done with it): refill it with iteration j + kStages.
+        issue(j + kStages, idx[0]);
+#pragma unroll
+        for (int k = 0; k < kStages; ++k)
+            if (st == k) gi_cur[k] = idx[0];
+#pragma unroll
+        for (int k = 0; k + 1 < kStages; ++k) idx[k] = idx[k + 1];
+        idx[kStages - 1] = point_of(j + 2 * kStages);
         if (have) {
             // dL/df = sum over the 2x2 slots (fixed order) of T a times the pixel's dL/dF.
             float acc[P];
@@ -251,19 +265,13 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
                 }
                 acc[C] += s_da[sl * kBatch + tid];
             }
-            float* out = partial + (size_t)(s_base[st * kBatch + tid] + (uint32_t)slot_base) * P;
+            float* out = partial + (size_t)(my_base + (uint32_t)slot_base) * P;
 #pragma unroll
             for (int k = 0; k < P; ++k) out[k] = acc[k];
         }
-        __syncthreads();
-        // Slot st is free: refill it with iteration j + kStages.
-        issue(j + kStages, idx[0]);
-#pragma unroll
-        for (int k = 0; k < kStages; ++k)
-            if (st == k) gi_cur[k] = idx[0];
-#pragma unroll
-        for (int k = 0; k + 1 < kStages; ++k) idx[k] = idx[k + 1];
-        idx[kStages - 1] = point_of(j + 2 * kStages);
+        // No third barrier: the next iteration's writes to shared memory (this
+        // thread's own contribution columns, the staging arrays and mask bits)
+        // come after its first barrier, which every reader here precedes.
     }
     cp_async_wait<0>();
     if (tid == 0) trace_tile(trace, tile, 1, t_start, c_start);

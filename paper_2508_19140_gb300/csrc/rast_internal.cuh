@@ -160,8 +160,9 @@ struct Bufs {
     uint32_t* valC[2];
     float* partial;       // backward per-copy partial gradients
     // radix sort scratch
-    uint32_t* hist;       // [bins][hist_tiles]
-    uint32_t* bin_total;  // [passes][512]
+    uint32_t* sort_ghist;     // [passes][bins] digit counts
+    uint32_t* sort_counters;  // [4] tile counters of the passes
+    uint32_t* sort_status;    // [passes][tiles][bins] look-back words
     // per tile / pixel
     uint2* ranges;
     uint32_t* order;      // tiles, heaviest list first
@@ -172,7 +173,6 @@ struct Bufs {
     WsHeader* hdr;
     CUtensorMap rec_map;  // records as a [n_points][rec_words] u32 tensor, one-row boxes (TMA gather4)
     int64_t copy_cap;
-    int64_t hist_tiles;
     int64_t blk_cap;
 };
 
@@ -183,17 +183,24 @@ struct SortPlan {
     int shift[8];
 };
 SortPlan make_sort_plan(int bits);
-int64_t sort_hist_tiles(int64_t cap);
+// Look-back words one sort with this plan needs for `cap` elements.
+int64_t sort_status_words(const SortPlan& plan, int64_t cap);
+
+struct SortScratch {
+    uint32_t* ghist;     // [4][512]
+    uint32_t* counters;  // [4]
+    uint32_t* status;    // sort_status_words()
+    uint32_t* err;       // workspace error word
+};
 
 cudaError_t launch_project(const ViewTable& vt, const Bufs& b, cudaStream_t s);
 // Stable LSD radix sort of (key, val) pairs in keys[0]/vals[0] using keys[1]/vals[1]
-// as scratch; count from d_n (device) if non-null else n. Returns the index (0/1)
-// of the buffer that holds the result.
-// names: profiling names of the hist, scan and scatter kernels.
-cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n,
-                       int64_t cap, const SortPlan& plan, uint32_t* hist, int64_t hist_tiles,
-                       uint32_t* bin_total, cudaStream_t s, int* result_buf,
-                       const char* const names[3]);
+// as scratch; count from d_n (device) if non-null else n (at most cap). Sets
+// *result_buf to the index (0/1) of the buffer that holds the result.
+// names: profiling names of the digit-count kernel and of the sweep passes.
+cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n, int64_t cap,
+                       const SortPlan& plan, const SortScratch& sc, cudaStream_t s, int* result_buf,
+                       const char* const names[2]);
 cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
                              cudaStream_t s);
 cudaError_t launch_ranges(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_tiles,

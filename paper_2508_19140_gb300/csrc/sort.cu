@@ -1,4 +1,4 @@
-// K4: stable LSD radix sort of (u32 key, u32 value) pairs.
+// K4: stable LSD radix sort of (u32 key, u32 value) pairs, one kernel per digit.
 //
 // The split sort of Sec. 3.2 ("Tiled Rendering") runs this twice: first over
 // the points by depth key, then over the point-tile copies by tile id. Both
@@ -6,19 +6,26 @@
 // point index, and what keeps the depth order inside every tile after the
 // second sort.
 //
-// One pass per digit of up to 9 bits, three kernels per pass
-// (reduce-then-scan):
-//   hist    per 4096-key tile, a digit histogram -> hist[digit][tile], and the
-//           per-digit totals (integer atomics, order-free);
-//   scan    one block per digit: exclusive scan over tiles, offset by the
-//           totals of all smaller digits;
-//   scatter per tile: stable in-tile rank (warp match + per-warp counters in
-//           ascending warp order), staged in shared memory in digit order, then
-//           written out in runs so consecutive threads write consecutive
-//           addresses.
-// The element count may live on the device (copies are counted on the GPU);
-// the kernels are persistent over tiles so one launch shape serves any count up
-// to the capacity, with no host synchronisation.
+// Structure (single-sweep LSD with decoupled look-back):
+//   k_digit_hist  one read of all keys counts the digits of every pass at once
+//                 (digit counts do not depend on the order), and clears the
+//                 per-pass tile counters and look-back status words;
+//   k_sweep       per pass, persistent CTAs take 4096-key tiles in input order
+//                 from an atomic counter, rank each key stably inside the tile
+//                 (one ballot per digit bit gives each lane the mask of lanes
+//                 holding the same digit; warps counted in ascending order),
+//                 publish the tile's per-digit counts, and add the counts of
+//                 all earlier tiles by looking back over their published words
+//                 (a tile whose whole prefix is known publishes it, so walks are
+//                 short). Keys are then staged in shared memory in digit order
+//                 and written out in runs.
+// A tile only waits on tiles that running CTAs took before it, so the waits
+// always end; each wait is still bounded, and on expiry the kernel raises the
+// timeout bit of the workspace error word and carries on with a zero prefix
+// instead of spinning on. The element count may live on the device (copies
+// are counted on the GPU): launch shapes depend only on the capacity.
+#include <cuda/atomic>
+
 #include "rast_internal.cuh"
 
 namespace rast {
@@ -28,6 +35,9 @@ constexpr int kThreads = 256;
 constexpr int kIPT = 16;
 constexpr int kSortTile = kThreads * kIPT;  // 4096 keys per tile
 constexpr int kWarpItems = 32 * kIPT;       // 512 keys per warp
+constexpr uint32_t kFlagAgg = 1u << 30;     // tile count published
+constexpr uint32_t kFlagPrefix = 2u << 30;  // inclusive prefix over tiles 0..t published
+constexpr uint32_t kValueMask = (1u << 30) - 1;
 
 int num_sms() {
     static int n = 0;
@@ -42,49 +52,6 @@ int num_sms() {
 
 __device__ __forceinline__ int64_t read_count(int64_t n_host, const uint32_t* d_n) {
     return d_n ? (int64_t)(*d_n) : n_host;
-}
-
-template <int BITS>
-__global__ void __launch_bounds__(kThreads) k_radix_hist(const uint32_t* __restrict__ keys,
-                                                         int64_t n_host, const uint32_t* d_n,
-                                                         int shift, uint32_t* __restrict__ hist,
-                                                         int64_t hist_tiles,
-                                                         uint32_t* __restrict__ bin_total) {
-    constexpr int BINS = 1 << BITS;
-    __shared__ uint32_t s_h[8 * BINS];
-    const int64_t n = read_count(n_host, d_n);
-    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    const int warp = threadIdx.x >> 5;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        for (int i = threadIdx.x; i < 8 * BINS; i += kThreads) s_h[i] = 0;
-        __syncthreads();
-        const int64_t base = tile * kSortTile;
-        if (base + kSortTile <= n) {
-            const uint4* k4 = reinterpret_cast<const uint4*>(keys + base);
-#pragma unroll
-            for (int j = 0; j < kIPT / 4; ++j) {
-                const uint4 q = k4[j * kThreads + threadIdx.x];
-                atomicAdd(&s_h[warp * BINS + ((q.x >> shift) & (BINS - 1))], 1u);
-                atomicAdd(&s_h[warp * BINS + ((q.y >> shift) & (BINS - 1))], 1u);
-                atomicAdd(&s_h[warp * BINS + ((q.z >> shift) & (BINS - 1))], 1u);
-                atomicAdd(&s_h[warp * BINS + ((q.w >> shift) & (BINS - 1))], 1u);
-            }
-        } else {
-            for (int j = 0; j < kIPT; ++j) {
-                const int64_t idx = base + (int64_t)j * kThreads + threadIdx.x;
-                if (idx < n) atomicAdd(&s_h[warp * BINS + ((keys[idx] >> shift) & (BINS - 1))], 1u);
-            }
-        }
-        __syncthreads();
-        for (int bin = threadIdx.x; bin < BINS; bin += kThreads) {
-            uint32_t c = 0;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) c += s_h[w * BINS + bin];
-            hist[(int64_t)bin * hist_tiles + tile] = c;
-            if (c) atomicAdd(&bin_total[bin], c);
-        }
-        __syncthreads();
-    }
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
@@ -121,37 +88,42 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp
     return res;
 }
 
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist, int64_t hist_tiles,
-                                                     const uint32_t* __restrict__ bin_total,
-                                                     int64_t n_host, const uint32_t* d_n) {
-    __shared__ uint32_t s_warp[33];
-    const int bin = blockIdx.x;
+// Digit counts of every pass with one read of the keys; clears the tile
+// counters and the look-back words the passes will use.
+template <int BITS>
+__global__ void __launch_bounds__(kThreads) k_digit_hist(const uint32_t* __restrict__ keys, int64_t n_host,
+                                                         const uint32_t* d_n, int passes,
+                                                         uint32_t* __restrict__ ghist,
+                                                         uint32_t* __restrict__ counters,
+                                                         uint32_t* __restrict__ status, int64_t tiles_cap) {
+    constexpr int BINS = 1 << BITS;
+    __shared__ uint32_t s_h[4 * BINS];
     const int64_t n = read_count(n_host, d_n);
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    uint32_t part = 0;
-    for (int b = threadIdx.x; b < bin; b += 1024) part += bin_total[b];
-    uint32_t base;
-    block_excl_scan<1024>(part, s_warp, base);
-    const int64_t per = (ntiles + 1023) / 1024;
-    const int64_t lo = threadIdx.x * per;
-    const int64_t hi = lo + per < ntiles ? lo + per : ntiles;
-    uint32_t* row = hist + (int64_t)bin * hist_tiles;
-    uint32_t s = 0;
-    for (int64_t t = lo; t < hi; ++t) s += row[t];
-    uint32_t tot;
-    uint32_t run = base + block_excl_scan<1024>(s, s_warp, tot);
-    for (int64_t t = lo; t < hi; ++t) {
-        const uint32_t c = row[t];
-        row[t] = run;
-        run += c;
+    for (int i = threadIdx.x; i < passes * BINS; i += kThreads) s_h[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 4) counters[threadIdx.x] = 0;
+    for (int p = 0; p < passes; ++p) {
+        uint32_t* st = status + (int64_t)p * tiles_cap * BINS;
+        const int64_t words = ntiles * BINS;
+        for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < words; i += (int64_t)gridDim.x * kThreads)
+            st[i] = 0;
     }
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const uint32_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * BINS + ((k >> (p * BITS)) & (BINS - 1))], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * BINS; i += kThreads)
+        if (s_h[i]) atomicAdd(&ghist[i], s_h[i]);
 }
 
 template <int BITS>
-__global__ void __launch_bounds__(kThreads) k_radix_scatter(
+__global__ void __launch_bounds__(kThreads) k_sweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n_host, const uint32_t* d_n, int shift,
-    const uint32_t* __restrict__ hist, int64_t hist_tiles) {
+    const uint32_t* __restrict__ ghist_pass, uint32_t* __restrict__ counter, uint32_t* __restrict__ status,
+    uint32_t* __restrict__ err) {
     constexpr int BINS = 1 << BITS;
     constexpr int VPT = BINS > kThreads ? BINS / kThreads : 1;
     extern __shared__ uint32_t smem[];
@@ -160,13 +132,39 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
     uint32_t* s_whist = s_vals + kSortTile;        // 8 * BINS: per-warp counts, then prefixes
     uint32_t* s_excl = s_whist + 8 * BINS;         // BINS: tile-local digit starts
     uint32_t* s_gbase = s_excl + BINS;             // BINS: global digit starts of this tile
-    uint32_t* s_warp = s_gbase + BINS;             // 33
+    uint32_t* s_goff = s_gbase + BINS;             // BINS: global digit starts of the pass
+    uint32_t* s_warp = s_goff + BINS;              // 33
+    uint32_t* s_tile = s_warp + 33;                // 1
     const int64_t n = read_count(n_host, d_n);
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
 
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // Global start of every digit in this pass.
+    {
+        uint32_t tot[VPT];
+        uint32_t local = 0;
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            const int bin = threadIdx.x * VPT + q;
+            tot[q] = bin < BINS ? ghist_pass[bin] : 0u;
+            local += tot[q];
+        }
+        uint32_t all;
+        uint32_t ex = block_excl_scan<kThreads>(local, s_warp, all);
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            const int bin = threadIdx.x * VPT + q;
+            if (bin < BINS) s_goff[bin] = ex;
+            ex += tot[q];
+        }
+    }
+
+    for (;;) {
+        if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1u);
+        __syncthreads();
+        const int64_t tile = *s_tile;
+        if (tile >= ntiles) break;
         const int64_t base = tile * kSortTile;
         const int64_t wbase = base + warp * kWarpItems;
         uint32_t k[kIPT], v[kIPT];
@@ -178,7 +176,6 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
             v[r] = ok ? vin[idx] : 0u;
         }
         for (int i = threadIdx.x; i < 8 * BINS; i += kThreads) s_whist[i] = 0;
-        for (int b = threadIdx.x; b < BINS; b += kThreads) s_gbase[b] = hist[(int64_t)b * hist_tiles + tile];
         __syncthreads();
 
         // Stable rank inside the warp's 512 keys: rounds in input order, lanes
@@ -190,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
             const bool ok = idx < n;
             const uint32_t d = ok ? ((k[r] >> shift) & (BINS - 1)) : 0u;
             // Lanes holding the same digit: one ballot per digit bit (and one
-            // for validity) instead of a match instruction.
+            // for validity).
             uint32_t peers = __ballot_sync(0xffffffffu, ok);
             if (!ok) peers = ~peers;
 #pragma unroll
@@ -208,7 +205,8 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
         }
         __syncthreads();
 
-        // Per digit: warp prefixes (ascending warp = ascending input order) and totals.
+        // Per digit: warp prefixes (ascending warp = ascending input order) and
+        // the tile's count.
         uint32_t tot[VPT];
 #pragma unroll
         for (int q = 0; q < VPT; ++q) {
@@ -223,6 +221,44 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
                 }
             }
             tot[q] = run;
+        }
+        // Publish the tile's counts, then look back for the counts of all
+        // earlier tiles and publish the inclusive prefix.
+        uint32_t* my = status + tile * BINS;
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            const int bin = threadIdx.x * VPT + q;
+            if (bin < BINS) {
+                cuda::atomic_ref<uint32_t, cuda::thread_scope_device> w(my[bin]);
+                w.store((tile == 0 ? kFlagPrefix : kFlagAgg) | tot[q], cuda::memory_order_relaxed);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            const int bin = threadIdx.x * VPT + q;
+            if (bin >= BINS) continue;
+            uint32_t excl = 0;
+            for (int64_t t = tile - 1; t >= 0; --t) {
+                cuda::atomic_ref<uint32_t, cuda::thread_scope_device> w(status[t * BINS + bin]);
+                uint32_t val = w.load(cuda::memory_order_relaxed);
+                uint32_t spins = 0;
+                while ((val >> 30) == 0u) {
+                    if (++spins > (1u << 22)) {  // a predecessor never published: give up
+                        atomicOr(err, kErrTimeout);
+                        val = kFlagPrefix;
+                        break;
+                    }
+                    __nanosleep(64);
+                    val = w.load(cuda::memory_order_relaxed);
+                }
+                excl += val & kValueMask;
+                if ((val & kFlagPrefix) != 0u) break;
+            }
+            if (tile != 0) {
+                cuda::atomic_ref<uint32_t, cuda::thread_scope_device> w(my[bin]);
+                w.store(kFlagPrefix | (excl + tot[q]), cuda::memory_order_relaxed);
+            }
+            s_gbase[bin] = s_goff[bin] + excl;
         }
         uint32_t local = 0;
 #pragma unroll
@@ -262,43 +298,51 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
 }
 
 template <int BITS>
-size_t scatter_smem() {
+size_t sweep_smem() {
     constexpr int BINS = 1 << BITS;
-    return sizeof(uint32_t) * (2 * kSortTile + 8 * BINS + 2 * BINS + 33);
+    return sizeof(uint32_t) * (2 * kSortTile + 8 * BINS + 3 * BINS + 33 + 1);
 }
 
 template <int BITS>
-cudaError_t sort_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
-                      int64_t n, const uint32_t* d_n, int64_t cap, int shift, uint32_t* hist,
-                      int64_t hist_tiles, uint32_t* bin_total, cudaStream_t s,
-                      const char* const names[3]) {
+cudaError_t sort_t(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n, int64_t cap,
+                   const SortPlan& plan, const SortScratch& sc, cudaStream_t s, int* result_buf,
+                   const char* const names[2]) {
+    constexpr int BINS = 1 << BITS;
     static bool attr_set = false;
-    const size_t smem = scatter_smem<BITS>();
+    const size_t smem = sweep_smem<BITS>();
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<BITS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_sweep<BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int64_t tiles_cap = (cap + kSortTile - 1) / kSortTile;
-    if (tiles_cap == 0) return cudaSuccess;
     const int sms = num_sms();
-    const unsigned gh = (unsigned)(tiles_cap < (int64_t)sms * 8 ? tiles_cap : (int64_t)sms * 8);
-    const unsigned gs = (unsigned)(tiles_cap < (int64_t)sms * 4 ? tiles_cap : (int64_t)sms * 4);
+    cudaError_t e = cudaMemsetAsync(sc.ghist, 0, sizeof(uint32_t) * plan.passes * BINS, s);
+    if (e != cudaSuccess) return e;
     {
         ProfScope ps(names[0], s);
-        k_radix_hist<BITS><<<gh, kThreads, 0, s>>>(kin, n, d_n, shift, hist, hist_tiles, bin_total);
+        int64_t g = (cap + kThreads * 16 - 1) / (kThreads * 16);
+        if (g > (int64_t)sms * 4) g = (int64_t)sms * 4;
+        if (g < 1) g = 1;
+        k_digit_hist<BITS><<<(unsigned)g, kThreads, 0, s>>>(keys[0], n, d_n, plan.passes, sc.ghist,
+                                                           sc.counters, sc.status, tiles_cap);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    {
+    const unsigned gs = (unsigned)(tiles_cap < (int64_t)sms * 2 ? tiles_cap : (int64_t)sms * 2);
+    int cur = 0;
+    for (int k = 0; k < plan.passes; ++k) {
         ProfScope ps(names[1], s);
-        k_radix_scan<<<1 << BITS, 1024, 0, s>>>(hist, hist_tiles, bin_total, n, d_n);
+        k_sweep<BITS><<<gs, kThreads, smem, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, d_n,
+                                                 plan.shift[k], sc.ghist + k * BINS, sc.counters + k,
+                                                 sc.status + (int64_t)k * tiles_cap * BINS, sc.err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
     }
-    {
-        ProfScope ps(names[2], s);
-        k_radix_scatter<BITS><<<gs, kThreads, smem, s>>>(kin, vin, kout, vout, n, d_n, shift, hist,
-                                                          hist_tiles);
-    }
-    return cudaGetLastError();
+    *result_buf = cur;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -322,41 +366,25 @@ SortPlan make_sort_plan(int bits) {
     return p;
 }
 
-int64_t sort_hist_tiles(int64_t cap) { return (cap + kSortTile - 1) / kSortTile; }
+int64_t sort_status_words(const SortPlan& plan, int64_t cap) {
+    if (plan.passes == 0) return 0;
+    return (int64_t)plan.passes * ((cap + kSortTile - 1) / kSortTile) * (1 << plan.digit_bits[0]);
+}
 
-cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n,
-                       int64_t cap, const SortPlan& plan, uint32_t* hist, int64_t hist_tiles,
-                       uint32_t* bin_total, cudaStream_t s, int* result_buf,
-                       const char* const names[3]) {
-    int cur = 0;
+cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n, int64_t cap,
+                       const SortPlan& plan, const SortScratch& sc, cudaStream_t s, int* result_buf,
+                       const char* const names[2]) {
     *result_buf = 0;
     if (plan.passes == 0 || cap == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(bin_total, 0, sizeof(uint32_t) * 512 * plan.passes, s);
-    if (e != cudaSuccess) return e;
-    for (int k = 0; k < plan.passes; ++k) {
-        uint32_t* bt = bin_total + 512 * k;
-        const int nb = plan.digit_bits[k];
-        switch (nb) {
-#define RAST_PASS(B)                                                                              \
-    case B:                                                                                       \
-        e = sort_pass<B>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, d_n, cap,         \
-                         plan.shift[k], hist, hist_tiles, bt, s, names);                          \
-        break;
-            RAST_PASS(4)
-            RAST_PASS(5)
-            RAST_PASS(6)
-            RAST_PASS(7)
-            RAST_PASS(8)
-            RAST_PASS(9)
-#undef RAST_PASS
-            default:
-                return cudaErrorInvalidValue;
-        }
-        if (e != cudaSuccess) return e;
-        cur ^= 1;
+    switch (plan.digit_bits[0]) {
+        case 4: return sort_t<4>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
+        case 5: return sort_t<5>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
+        case 6: return sort_t<6>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
+        case 7: return sort_t<7>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
+        case 8: return sort_t<8>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
+        case 9: return sort_t<9>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
+        default: return cudaErrorInvalidValue;
     }
-    *result_buf = cur;
-    return cudaSuccess;
 }
 
 }  // namespace rast
