@@ -244,7 +244,8 @@ def run_ours(args, ws_, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    scene = scenes.make_scene(args.config, seed=1000 + args.config + 7919 * rank,
+    from paper_2508_19140_gb300.shard import rank_seed
+    scene = scenes.make_scene(args.config, seed=rank_seed(args.config, rank),
                               scale_points=args.scale_points)
     bf16 = scene.feat_dtype == "bf16"
     gauss = scene.mode == "gaussian"
