@@ -6,7 +6,7 @@
  * n_w-channel feature f_i; Sec. 2 "Rendering Feature Maps") are projected
  * through a pinhole camera, splatted as bilinear 2x2 footprints or as small
  * isotropic Gaussians (Sec. 3.2 "Rendering Points as Small Gaussians"), binned
- * into 16x16 tiles and sorted by (tile, depth, point index) (Sec. 3.2 "Tiled
+ * into 16x16 (or 8x8) tiles and sorted by (tile, depth, point index) (Sec. 3.2 "Tiled
  * Rendering", split sort), then alpha-blended front to back by Eq. 1 into a
  * feature image F (H x W x n_w), an alpha image and a depth image. The
  * backward pass implements the corrected gradient of the appendix (Eq. 2,
@@ -46,7 +46,7 @@ typedef enum {
     RAST_ERR_CAPACITY = 2,       /* workspace too small, or copies exceeded max_copies */
     RAST_ERR_CUDA = 3,           /* a CUDA runtime call failed */
     RAST_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up */
-    RAST_ERR_NOT_SUPPORTED = 5   /* channel count, tile size or mode not compiled in */
+    RAST_ERR_NOT_SUPPORTED = 5   /* channel count, tile size, blend depth or mode not compiled in */
 } rast_status_t;
 
 typedef enum { RAST_SPLAT_BILINEAR = 0, RAST_SPLAT_GAUSSIAN = 1 } rast_mode_t;
@@ -81,8 +81,10 @@ typedef struct {
 typedef struct {
     int32_t mode;          /* rast_mode_t */
     int32_t gauss_cov;     /* rast_gauss_cov_t */
-    int32_t tile;          /* tile edge in pixels: 16 */
-    int32_t blend_depth;   /* records staged per blend batch: 0 = default (256) */
+    int32_t tile;          /* tile edge in pixels: 16 (default) or 8; the images and gradients
+                              do not depend on it, only the work split does */
+    int32_t blend_depth;   /* records staged per blend batch: 0 = default (tile * tile, the
+                              only compiled value) */
     float t_min;           /* early termination: stop before T (1 - a) < t_min (1e-4) */
     float alpha_max;       /* alpha clamp (0.99) */
     float dilation;        /* screen-space dilation variance, Gaussian mode (0.16) */

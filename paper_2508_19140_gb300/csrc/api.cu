@@ -55,12 +55,12 @@ struct Plan {
     int partial_floats;
 };
 
-rast_status_t check_view(const rast_view_t& v, int pass) {
+rast_status_t check_view(const rast_view_t& v, int pass, int T) {
     const rast_points_t& p = v.pts;
     const rast_camera_t& c = v.cam;
     if (p.n < 0) return RAST_ERR_ARG;
     if (p.n > 0 && (!p.xyz || !p.opacity || !p.feat)) return RAST_ERR_ARG;
-    if (c.width < 1 || c.height < 1 || c.width > 65535 * kTile || c.height > 65535 * kTile)
+    if (c.width < 1 || c.height < 1 || c.width > 65535 * T || c.height > 65535 * T)
         return RAST_ERR_ARG;
     if (!(c.near_z > 0.f) || !(c.far_z > c.near_z) || !std::isfinite(c.far_z)) return RAST_ERR_ARG;
     const float* cf = &c.fx;
@@ -76,8 +76,8 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     if (!views || !o || n_views < 1 || n_views > kMaxViews) return RAST_ERR_ARG;
     if (o->mode != RAST_SPLAT_BILINEAR && o->mode != RAST_SPLAT_GAUSSIAN) return RAST_ERR_ARG;
     if (o->gauss_cov != RAST_GAUSS_EWA && o->gauss_cov != RAST_GAUSS_ISO_SCREEN) return RAST_ERR_ARG;
-    if (o->tile != kTile) return RAST_ERR_NOT_SUPPORTED;
-    if (o->blend_depth != 0 && o->blend_depth != kBatch) return RAST_ERR_NOT_SUPPORTED;
+    if (o->tile != 8 && o->tile != 16) return RAST_ERR_NOT_SUPPORTED;
+    if (o->blend_depth != 0 && o->blend_depth != o->tile * o->tile) return RAST_ERR_NOT_SUPPORTED;
     if (!(o->t_min >= 0.f) || !(o->alpha_max > 0.f && o->alpha_max < 1.f)) return RAST_ERR_ARG;
     if (!(o->dilation >= 0.f) || o->max_copies < 0) return RAST_ERR_ARG;
     const int C = views[0].pts.channels;
@@ -92,6 +92,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     vt.bf16 = dt == RAST_BF16;
     vt.mode = o->mode;
     vt.gauss_cov = o->gauss_cov;
+    vt.tile = o->tile;
     vt.t_min = o->t_min;
     vt.alpha_max = o->alpha_max;
     vt.dilation = o->dilation;
@@ -105,7 +106,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     for (int k = 0; k < n_views; ++k) {
         const rast_view_t& v = views[k];
         if (v.pts.channels != C || v.pts.feat_dtype != dt) return RAST_ERR_ARG;
-        rast_status_t st = check_view(v, pass);
+        rast_status_t st = check_view(v, pass, o->tile);
         if (st != RAST_OK) return st;
         ViewDev& d = vt.v[k];
         const rast_camera_t& c = v.cam;
@@ -116,8 +117,8 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
         d.far_z = c.far_z;
         d.W = c.width;
         d.H = c.height;
-        d.tiles_x = (c.width + kTile - 1) / kTile;
-        d.tiles_y = (c.height + kTile - 1) / kTile;
+        d.tiles_x = (c.width + o->tile - 1) / o->tile;
+        d.tiles_y = (c.height + o->tile - 1) / o->tile;
         d.key_base = f32_bits(c.near_z);
         d.key_cull = f32_bits(c.far_z) - f32_bits(c.near_z);
         if (d.key_cull > max_cull) max_cull = d.key_cull;
@@ -395,7 +396,7 @@ void rast_default_opts(rast_opts_t* o) {
     std::memset(o, 0, sizeof(*o));
     o->mode = RAST_SPLAT_BILINEAR;
     o->gauss_cov = RAST_GAUSS_EWA;
-    o->tile = kTile;
+    o->tile = kTileDefault;
     o->blend_depth = 0;
     o->t_min = 1e-4f;
     o->alpha_max = 0.99f;

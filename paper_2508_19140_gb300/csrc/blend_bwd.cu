@@ -39,38 +39,40 @@ __device__ __forceinline__ uint32_t block_max_u32(uint32_t x, uint32_t* s) {
 
 constexpr int kStages = 3;  // cp.async ring depth (batches in flight per CTA)
 
-template <int C, bool BF16>
+template <int TS, int C, bool BF16>
 constexpr size_t bilinear_bwd_smem() {
-    return sizeof(uint32_t) * kStages * kBatch * RecLayout<0, C, BF16>::words  // record ring
-           + sizeof(uint32_t) * kStages * kBatch                              // slot-base ring
-           + sizeof(float) * 4 * 2 * kBatch                                   // (T a, w dL/da) per slot
-           + sizeof(float) * kTilePix * C                                     // upstream dL/dF per pixel
+    return sizeof(uint32_t) * kStages * TS * TS * RecLayout<0, C, BF16>::words  // record ring
+           + sizeof(uint32_t) * kStages * TS * TS                              // slot-base ring
+           + sizeof(float) * 4 * 2 * TS * TS                                   // (T a, w dL/da) per slot
+           + sizeof(float) * TS * TS * C                                       // upstream dL/dF per pixel
            + 128;
 }
 
-template <int C, bool BF16>
-__global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
+template <int TS, int C, bool BF16>
+__global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec,
     const float* __restrict__ t_final, const uint32_t* __restrict__ last_in,
     const uint32_t* __restrict__ base, float* __restrict__ partial, uint2* __restrict__ cutoff,
     WsHeader* __restrict__ hdr, unsigned long long* __restrict__ trace) {
+    constexpr int NT = TS * TS;    // threads = pixels = records per batch
+    constexpr int MW = NT / 32;  // mask words per pixel
     const unsigned long long t_start = global_ns();
     const long long c_start = clock64();
     constexpr int P = C + 1;  // dfeat[C], dopacity
     constexpr int RW = RecLayout<0, C, BF16>::words;
     constexpr int FW = RecLayout<0, C, BF16>::feat_word;
     extern __shared__ __align__(128) uint32_t s_dyn[];
-    uint32_t* const s_ring = align128(s_dyn);                        // [kStages][kBatch][RW]
-    uint32_t* const s_base = s_ring + kStages * kBatch * RW;         // [kStages][kBatch]
-    float* const s_ta = reinterpret_cast<float*>(s_base + kStages * kBatch);  // [4][kBatch]
-    float* const s_da = s_ta + 4 * kBatch;                           // [4][kBatch]
-    float* const s_gF = s_da + 4 * kBatch;                           // [kTilePix][C]
-    __shared__ uint32_t s_mask[kTilePix][9];
-    __shared__ float s_w[4][kBatch];    // bilinear weight per slot
-    __shared__ float s_inv[4][kBatch];  // 1 / (1 - alpha) per slot
-    __shared__ float s_o[kBatch];       // opacity per record
-    __shared__ uint32_t s_anchor[kBatch];
+    uint32_t* const s_ring = align128(s_dyn);                        // [kStages][NT][RW]
+    uint32_t* const s_base = s_ring + kStages * NT * RW;         // [kStages][NT]
+    float* const s_ta = reinterpret_cast<float*>(s_base + kStages * NT);  // [4][NT]
+    float* const s_da = s_ta + 4 * NT;                           // [4][NT]
+    float* const s_gF = s_da + 4 * NT;                           // [NT][C]
+    __shared__ uint32_t s_mask[NT][MW + 1];
+    __shared__ float s_w[4][NT];    // bilinear weight per slot
+    __shared__ float s_inv[4][NT];  // 1 / (1 - alpha) per slot
+    __shared__ float s_o[NT];       // opacity per record
+    __shared__ uint32_t s_anchor[NT];
     __shared__ uint32_t s_red;
 
     const int64_t tile = order[blockIdx.x];
@@ -78,8 +80,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int lx = tid & 15, ly = tid >> 4;
-    const int px = tx * kTile + lx, py = ty * kTile + ly;
+    const int lx = tid & (TS - 1), ly = tid / TS;
+    const int px = tx * TS + lx, py = ty * TS + ly;
     const bool inside = px < V.W && py < V.H;
     const uint2 rg = ranges[tile];
     const float amax = vt.alpha_max;
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     // Each thread clears its own mask row; the barriers inside block_max_u32
     // order these stores before any thread sets bits in another pixel's row.
 #pragma unroll
-    for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
+    for (int w = 0; w < MW; ++w) s_mask[tid][w] = 0;
     const uint32_t maxlast = block_max_u32(last, &s_red);
     if (tid == 0 && maxlast) atomicAdd(&hdr->needed_bwd, (unsigned long long)maxlast);
     if (maxlast == 0) {
@@ -116,23 +118,23 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     float Sg = 0.f, SD = 0.f;
     const float Kd = -gA * Tfin;  // constant part of the 1/(1-a) term
     const uint32_t end = rg.x + maxlast;
-    const uint32_t nb = (maxlast - 1) / kBatch + 1;  // batches, processed last to first
+    const uint32_t nb = (maxlast - 1) / NT + 1;  // batches, processed last to first
 
     // Iteration j handles batch nb-1-j. Thread t copies record t of each batch
     // (and its slot base); idx[k] = point of iteration j + kStages + k.
     auto point_of = [&](uint32_t j) -> uint32_t {
         if (j >= nb) return 0xffffffffu;
-        const uint32_t q = rg.x + (nb - 1 - j) * kBatch + tid;
+        const uint32_t q = rg.x + (nb - 1 - j) * NT + tid;
         return q < end ? pts[q] : 0xffffffffu;
     };
     auto issue = [&](uint32_t j, uint32_t gi) {
         if (gi != 0xffffffffu) {
             const int st = (int)(j % kStages);
-            uint32_t* dst = s_ring + ((size_t)st * kBatch + tid) * RW;
+            uint32_t* dst = s_ring + ((size_t)st * NT + tid) * RW;
             const uint32_t* src = rec + (size_t)gi * RW;
 #pragma unroll
             for (int k = 0; k < RW; k += 4) cp_async16(dst + k, src + k);
-            cp_async4(s_base + st * kBatch + tid, base + gi);
+            cp_async4(s_base + st * NT + tid, base + gi);
         }
         cp_async_commit();
     };
@@ -150,14 +152,14 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
     for (uint32_t j = 0; j < nb; ++j) {
         const uint32_t bi = nb - 1 - j;
         const int st = (int)(j % kStages);
-        const uint32_t* ring = s_ring + (size_t)st * kBatch * RW;
-        const uint32_t rel0 = bi * kBatch;
+        const uint32_t* ring = s_ring + (size_t)st * NT * RW;
+        const uint32_t rel0 = bi * NT;
         const uint32_t q = rg.x + rel0 + tid;
         const bool have = q < end;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            s_ta[k * kBatch + tid] = 0.f;
-            s_da[k * kBatch + tid] = 0.f;
+            s_ta[k * NT + tid] = 0.f;
+            s_da[k * NT + tid] = 0.f;
         }
         cp_async_wait<kStages - 1>();
         int slot_base = 0, X0 = 0, Y0 = 0;
@@ -175,23 +177,23 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
             s_inv[1][tid] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w1), amax)));
             s_inv[2][tid] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w2), amax)));
             s_inv[3][tid] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w3), amax)));
-            X0 = bg.i0 - tx * kTile;
-            Y0 = bg.j0 - ty * kTile;
+            X0 = bg.i0 - tx * TS;
+            Y0 = bg.j0 - ty * TS;
             s_anchor[tid] = (uint32_t)(X0 + 1) | ((uint32_t)(Y0 + 1) << 8);
             const uint32_t bit = 1u << lane;
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
                 const int Y = Y0 + dy;
-                if ((unsigned)Y >= (unsigned)kTile) continue;
+                if ((unsigned)Y >= (unsigned)TS) continue;
 #pragma unroll
                 for (int dx = 0; dx < 2; ++dx) {
                     const int X = X0 + dx;
-                    if ((unsigned)X < (unsigned)kTile) atomicOr(&s_mask[Y * kTile + X][warp], bit);
+                    if ((unsigned)X < (unsigned)TS) atomicOr(&s_mask[Y * TS + X][warp], bit);
                 }
             }
             // The point's tile rect (as the projection computed it) and this tile's rank in it.
-            const int tx0 = max(bg.i0, 0) / kTile, tx1 = min(bg.i0 + 1, V.W - 1) / kTile;
-            const int ty0 = max(bg.j0, 0) / kTile;
+            const int tx0 = max(bg.i0, 0) / TS, tx1 = min(bg.i0 + 1, V.W - 1) / TS;
+            const int ty0 = max(bg.j0, 0) / TS;
             slot_base = (ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0);
             if (q + 1 == end) {
                 uint32_t gi_last = gi_cur[0];
@@ -204,8 +206,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
         __syncthreads();
         if (inside && last > rel0) {
             // One loop over the set bits of the pixel's mask, last to first.
-            int w = 7;
-            uint32_t m = s_mask[tid][7];
+            int w = MW - 1;
+            uint32_t m = s_mask[tid][MW - 1];
 #pragma unroll 1
             while (true) {
                 while (m == 0 && w > 0) m = s_mask[tid][--w];
@@ -233,13 +235,13 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
                 Sg = fmaf(ta, fdot, Sg);
                 SD = fmaf(ta, z, SD);
                 T = Tk;
-                s_ta[slot * kBatch + r] = ta;
-                s_da[slot * kBatch + r] = (ow <= amax) ? wgt * dalpha : 0.f;
+                s_ta[slot * NT + r] = ta;
+                s_da[slot * NT + r] = (ow <= amax) ? wgt * dalpha : 0.f;
             }
         }
 #pragma unroll
-        for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
-        const uint32_t my_base = s_base[st * kBatch + tid];  // read before the slot is refilled
+        for (int w = 0; w < MW; ++w) s_mask[tid][w] = 0;
+        const uint32_t my_base = s_base[st * NT + tid];  // read before the slot is refilled
         __syncthreads();
         // Slot st is free (every pixel is done with it): refill it with iteration j + kStages.
         issue(j + kStages, idx[0]);
@@ -257,13 +259,13 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
 #pragma unroll
             for (int sl = 0; sl < 4; ++sl) {
                 const int X = X0 + (sl & 1), Y = Y0 + (sl >> 1);
-                const float ta = s_ta[sl * kBatch + tid];
-                if ((unsigned)X < (unsigned)kTile && (unsigned)Y < (unsigned)kTile) {
-                    const float* gp = s_gF + (Y * kTile + X) * C;
+                const float ta = s_ta[sl * NT + tid];
+                if ((unsigned)X < (unsigned)TS && (unsigned)Y < (unsigned)TS) {
+                    const float* gp = s_gF + (Y * TS + X) * C;
 #pragma unroll
                     for (int c = 0; c < C; ++c) acc[c] += ta * gp[c];
                 }
-                acc[C] += s_da[sl * kBatch + tid];
+                acc[C] += s_da[sl * NT + tid];
             }
             float* out = partial + (size_t)(my_base + (uint32_t)slot_base) * P;
 #pragma unroll
@@ -279,7 +281,6 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_bilinear(
 
 // ---------------------------------------------------------------- Gaussian
 
-constexpr int kGBatch = 128;  // records per backward batch (shared-memory bound)
 
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
@@ -287,19 +288,23 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
-template <int C, bool BF16>
-__global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
+template <int TS, int C, bool BF16>
+__global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec,
     const float* __restrict__ t_final, const uint32_t* __restrict__ last_in,
     const uint32_t* __restrict__ base, float* __restrict__ partial, uint2* __restrict__ cutoff,
     WsHeader* __restrict__ hdr) {
+    constexpr int NT = TS * TS;
+    constexpr int NW = NT / 32;                   // warps = 8x4 sub-tiles
+    constexpr int WPR = TS / 8;                    // sub-tiles per row
+    constexpr int kGBatch = NT >= 256 ? 128 : NT;  // records per backward batch
     constexpr int P = C + 7;  // dfeat[C], do, du, dv, dca, dcb, dcc, dz
     __shared__ float s_um[kGBatch], s_vm[kGBatch], s_o[kGBatch], s_z[kGBatch];
     __shared__ float s_ca[kGBatch], s_cb[kGBatch], s_cc[kGBatch];
     __shared__ int4 s_box[kGBatch];
     __shared__ float s_f[C][kGBatch];
-    extern __shared__ float s_contrib[];  // [8 warps][P][kGBatch]
+    extern __shared__ float s_contrib[];  // [NW warps][P][kGBatch]
     __shared__ uint32_t s_red;
 
     const int64_t tile = order[blockIdx.x];
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int sx0 = tx * kTile + (warp & 1) * 8, sy0 = ty * kTile + (warp >> 1) * 4;
+    const int sx0 = tx * TS + (warp % WPR) * 8, sy0 = ty * TS + (warp / WPR) * 4;
     const int px = sx0 + (lane & 7), py = sy0 + (lane >> 3);
     const bool inside = px < V.W && py < V.H;
     const uint2 rg = ranges[tile];
@@ -362,7 +367,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
         const uint32_t b0 = rg.x + rel0;
         const uint32_t bend = end < b0 + kGBatch ? end : b0 + kGBatch;
         const int nrec = (int)(bend - b0);
-        for (int k = tid; k < 8 * P * kGBatch; k += kBlendThreads) s_contrib[k] = 0.f;
+        for (int k = tid; k < NW * P * kGBatch; k += NT) s_contrib[k] = 0.f;
         const bool have = loader && b0 + tid < bend;
         const uint32_t my_bs = bs;
         int slot = 0;
@@ -381,8 +386,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
 #pragma unroll
             for (int c = 0; c < C; ++c) s_f[c][tid] = f[c];
             // tile rect of the in-image box, as the projection computed it
-            const int tx0 = max(bx.x0, 0) / kTile, tx1 = min(bx.x1, V.W - 1) / kTile;
-            const int ty0 = max(bx.y0, 0) / kTile;
+            const int tx0 = max(bx.x0, 0) / TS, tx1 = min(bx.x1, V.W - 1) / TS;
+            const int ty0 = max(bx.y0, 0) / TS;
             slot = (ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0);
             if (b0 + tid + 1 == end) cutoff[tile] = make_uint2(g.z, gi);
         }
@@ -473,7 +478,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_bwd_gauss(
             for (int k = 0; k < P; ++k) {
                 float acc = 0.f;
 #pragma unroll
-                for (int w = 0; w < 8; ++w) acc += s_contrib[(w * P + k) * kGBatch + tid];
+                for (int w = 0; w < NW; ++w) acc += s_contrib[(w * P + k) * kGBatch + tid];
                 out[k] = acc;
             }
         }
@@ -595,33 +600,35 @@ __global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const 
     if (V.d_scale) V.d_scale[i] = V.scale ? gs : 0.f;
 }
 
-template <int C, bool BF16>
+template <int TS, int C, bool BF16>
 cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     const unsigned grid = (unsigned)vt.tiles_total;
     if (vt.mode == 0) {
-        constexpr size_t smem = bilinear_bwd_smem<C, BF16>();
+        constexpr size_t smem = bilinear_bwd_smem<TS, C, BF16>();
         static bool set = false;
         if (!set) {
-            cudaError_t e = cudaFuncSetAttribute(k_blend_bwd_bilinear<C, BF16>,
+            cudaError_t e = cudaFuncSetAttribute(k_blend_bwd_bilinear<TS, C, BF16>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             set = true;
         }
         ProfScope ps("blend_bwd", s);
-        k_blend_bwd_bilinear<C, BF16><<<grid, kBlendThreads, smem, s>>>(
+        k_blend_bwd_bilinear<TS, C, BF16><<<grid, TS * TS, smem, s>>>(
             vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.cutoff, b.hdr,
             b.trace);
     } else {
-        constexpr size_t smem = sizeof(float) * 8 * (C + 7) * kGBatch;
+        constexpr int NT = TS * TS;
+        constexpr int GB = NT >= 256 ? 128 : NT;
+        constexpr size_t smem = sizeof(float) * (NT / 32) * (C + 7) * GB;
         static bool set = false;
         if (!set) {
-            cudaError_t e = cudaFuncSetAttribute(k_blend_bwd_gauss<C, BF16>,
+            cudaError_t e = cudaFuncSetAttribute(k_blend_bwd_gauss<TS, C, BF16>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             set = true;
         }
         ProfScope ps("blend_bwd", s);
-        k_blend_bwd_gauss<C, BF16><<<grid, kBlendThreads, smem, s>>>(
+        k_blend_bwd_gauss<TS, C, BF16><<<grid, TS * TS, smem, s>>>(
             vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.cutoff, b.hdr);
     }
     return cudaGetLastError();
@@ -629,7 +636,9 @@ cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts
 
 template <int C>
 cudaError_t launch_bwd_c(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
-    return vt.bf16 ? launch_bwd_t<C, true>(vt, b, pts, s) : launch_bwd_t<C, false>(vt, b, pts, s);
+    if (vt.tile == 8)
+        return vt.bf16 ? launch_bwd_t<8, C, true>(vt, b, pts, s) : launch_bwd_t<8, C, false>(vt, b, pts, s);
+    return vt.bf16 ? launch_bwd_t<16, C, true>(vt, b, pts, s) : launch_bwd_t<16, C, false>(vt, b, pts, s);
 }
 
 template <int C>

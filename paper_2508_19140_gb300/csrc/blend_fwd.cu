@@ -67,25 +67,27 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ r
 
 constexpr int kStages = 3;  // cp.async ring depth (batches in flight per CTA)
 
-template <int C, bool BF16>
+template <int TS, int C, bool BF16>
 constexpr size_t bilinear_fwd_smem() {
-    return sizeof(uint32_t) * kStages * kBatch * RecLayout<0, C, BF16>::words + 128;
+    return sizeof(uint32_t) * kStages * TS * TS * RecLayout<0, C, BF16>::words + 128;
 }
 
-template <int C, bool BF16>
-__global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
+template <int TS, int C, bool BF16>
+__global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec, float* __restrict__ t_final,
     uint32_t* __restrict__ last_out, WsHeader* __restrict__ hdr, unsigned long long* __restrict__ trace) {
+    constexpr int NT = TS * TS;       // threads = pixels = records per batch
+    constexpr int MW = NT / 32;     // mask words per pixel
     const unsigned long long t_start = global_ns();
     const long long c_start = clock64();
     constexpr int RW = RecLayout<0, C, BF16>::words;
     constexpr int FW = RecLayout<0, C, BF16>::feat_word;
     extern __shared__ __align__(128) uint32_t s_dyn[];
-    uint32_t* const s_ring = align128(s_dyn);  // [kStages][kBatch][RW] raw records
-    __shared__ uint32_t s_mask[kTilePix][9];   // 8 words + 1 pad: conflict-free row reads
-    __shared__ float s_alpha[4][kBatch];       // alpha of each record's 2x2 slots (FP32, pinned ops)
-    __shared__ uint32_t s_anchor[kBatch];      // tile-local anchor (X0 + 1) | (Y0 + 1) << 8
+    uint32_t* const s_ring = align128(s_dyn);  // [kStages][NT][RW] raw records
+    __shared__ uint32_t s_mask[NT][MW + 1];    // MW words + 1 pad: conflict-free row reads
+    __shared__ float s_alpha[4][NT];       // alpha of each record's 2x2 slots (FP32, pinned ops)
+    __shared__ uint32_t s_anchor[NT];      // tile-local anchor (X0 + 1) | (Y0 + 1) << 8
     __shared__ uint32_t s_maxstop;
 
     const int64_t tile = order[blockIdx.x];
@@ -93,12 +95,12 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int lx = tid & 15, ly = tid >> 4;
-    const int px = tx * kTile + lx, py = ty * kTile + ly;
+    const int lx = tid & (TS - 1), ly = tid / TS;
+    const int px = tx * TS + lx, py = ty * TS + ly;
     const bool inside = px < V.W && py < V.H;
     const uint2 rg = ranges[tile];
     const uint32_t len = rg.y - rg.x;
-    const uint32_t nbatch = (len + kBatch - 1) / kBatch;
+    const uint32_t nbatch = (len + NT - 1) / NT;
     const float amax = vt.alpha_max, tmin = vt.t_min;
 
     float T = 1.f, A = 0.f, Dp = 0.f;
@@ -108,18 +110,18 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
     uint32_t last = 0, stop = 0;
     bool done = !inside;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
+    for (int w = 0; w < MW; ++w) s_mask[tid][w] = 0;
     if (tid == 0) s_maxstop = 0;
 
     // Thread t copies record t of every batch. idx[k] = point index of batch
     // (j + kStages + k) while batch j is processed (loaded kStages batches ahead).
     auto point_of = [&](uint32_t j) -> uint32_t {
-        const uint32_t r = j * kBatch + tid;
+        const uint32_t r = j * NT + tid;
         return r < len ? pts[rg.x + r] : 0xffffffffu;
     };
     auto issue = [&](uint32_t j, uint32_t gi) {
         if (gi != 0xffffffffu) {
-            uint32_t* dst = s_ring + ((size_t)(j % kStages) * kBatch + tid) * RW;
+            uint32_t* dst = s_ring + ((size_t)(j % kStages) * NT + tid) * RW;
             const uint32_t* src = rec + (size_t)gi * RW;
 #pragma unroll
             for (int k = 0; k < RW; k += 4) cp_async16(dst + k, src + k);
@@ -136,9 +138,9 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
     }
 
     for (uint32_t j = 0; j < nbatch; ++j) {
-        const uint32_t* ring = s_ring + (size_t)(j % kStages) * kBatch * RW;
+        const uint32_t* ring = s_ring + (size_t)(j % kStages) * NT * RW;
         cp_async_wait<kStages - 1>();  // this thread's copy of batch j has landed
-        const uint32_t rel0 = j * kBatch;
+        const uint32_t rel0 = j * NT;
         if (rel0 + tid < len) {
             // Per record: the four fragment alphas of its 2x2 box (the ops of
             // bilin_weight and the clamp, so every pixel sees the same FP32 bits)
@@ -151,17 +153,17 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
             s_alpha[1][tid] = fminf(__fmul_rn(o, __fmul_rn(bg.a, by)), amax);
             s_alpha[2][tid] = fminf(__fmul_rn(o, __fmul_rn(ax, bg.b)), amax);
             s_alpha[3][tid] = fminf(__fmul_rn(o, __fmul_rn(bg.a, bg.b)), amax);
-            const int X0 = bg.i0 - tx * kTile, Y0 = bg.j0 - ty * kTile;
+            const int X0 = bg.i0 - tx * TS, Y0 = bg.j0 - ty * TS;
             s_anchor[tid] = (uint32_t)(X0 + 1) | ((uint32_t)(Y0 + 1) << 8);
             const uint32_t bit = 1u << lane;
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
                 const int Y = Y0 + dy;
-                if ((unsigned)Y >= (unsigned)kTile) continue;
+                if ((unsigned)Y >= (unsigned)TS) continue;
 #pragma unroll
                 for (int dx = 0; dx < 2; ++dx) {
                     const int X = X0 + dx;
-                    if ((unsigned)X < (unsigned)kTile) atomicOr(&s_mask[Y * kTile + X][warp], bit);
+                    if ((unsigned)X < (unsigned)TS) atomicOr(&s_mask[Y * TS + X][warp], bit);
                 }
             }
         }
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
             uint32_t m = s_mask[tid][0];
 #pragma unroll 1
             while (true) {
-                while (m == 0 && w < 7) m = s_mask[tid][++w];
+                while (m == 0 && w < MW - 1) m = s_mask[tid][++w];
                 if (m == 0) break;
                 const int r = w * 32 + __ffs(m) - 1;
                 m &= m - 1;
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
             }
         }
 #pragma unroll
-        for (int w = 0; w < 8; ++w) s_mask[tid][w] = 0;
+        for (int w = 0; w < MW; ++w) s_mask[tid][w] = 0;
         __syncthreads();
         // Slot j % kStages is free: refill it with batch j + kStages.
         issue(j + kStages, idx[0]);
@@ -233,17 +235,17 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_bilinear(
     }
 }
 
-constexpr int kGroups = kBatch / 32;
-
-template <int C, bool BF16>
-__global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
+template <int TS, int C, bool BF16>
+__global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec, float* __restrict__ t_final,
     uint32_t* __restrict__ last_out, WsHeader* __restrict__ hdr) {
-    __shared__ float s_um[kBatch], s_vm[kBatch], s_o[kBatch], s_z[kBatch];
-    __shared__ float s_ca[kBatch], s_cb[kBatch], s_cc[kBatch];
-    __shared__ int4 s_box[kBatch];
-    __shared__ float s_f[C][kBatch];
+    constexpr int NT = TS * TS;
+    constexpr int WPR = TS / 8;      // warps per row of 8x4 sub-tiles
+    __shared__ float s_um[NT], s_vm[NT], s_o[NT], s_z[NT];
+    __shared__ float s_ca[NT], s_cb[NT], s_cc[NT];
+    __shared__ int4 s_box[NT];
+    __shared__ float s_f[C][NT];
     __shared__ uint32_t s_maxstop;
 
     const int64_t tile = order[blockIdx.x];
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // warp -> 8x4 sub-tile
-    const int sx0 = tx * kTile + (warp & 1) * 8, sy0 = ty * kTile + (warp >> 1) * 4;
+    const int sx0 = tx * TS + (warp % WPR) * 8, sy0 = ty * TS + (warp / WPR) * 4;
     const int px = sx0 + (lane & 7), py = sy0 + (lane >> 3);
     const bool inside = px < V.W && py < V.H;
     const uint2 rg = ranges[tile];
@@ -279,10 +281,10 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
             load_features<C, BF16>(rp + FW, f);
         }
     }
-    uint32_t gi_next = (rg.x + kBatch + tid < rg.y) ? pts[rg.x + kBatch + tid] : 0u;
+    uint32_t gi_next = (rg.x + NT + tid < rg.y) ? pts[rg.x + NT + tid] : 0u;
     __syncthreads();
 
-    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBatch) {
+    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += NT) {
         if (b0 + tid < rg.y) {
             const float um = __fsub_rn(__uint_as_float(g.x), 0.5f);
             const float vm = __fsub_rn(__uint_as_float(g.y), 0.5f);
@@ -300,20 +302,20 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
         }
         if (__syncthreads_count(!done) == 0) break;
         {
-            const uint32_t qn = b0 + kBatch + tid;
+            const uint32_t qn = b0 + NT + tid;
             if (qn < rg.y) {
                 const uint32_t* rp = rec + (size_t)gi_next * RW;
                 g = *reinterpret_cast<const uint4*>(rp);
                 h = *reinterpret_cast<const uint4*>(rp + 4);
                 load_features<C, BF16>(rp + FW, f);
             }
-            gi_next = (qn + kBatch < rg.y) ? pts[qn + kBatch] : 0u;
+            gi_next = (qn + NT < rg.y) ? pts[qn + NT] : 0u;
         }
-        const int nrec = (int)min((uint32_t)kBatch, rg.y - b0);
+        const int nrec = (int)min((uint32_t)NT, rg.y - b0);
         const uint32_t rel0 = b0 - rg.x;
         if (!__all_sync(0xffffffffu, done)) {
 #pragma unroll 1
-            for (int grp = 0; grp < kGroups; ++grp) {
+            for (int grp = 0; grp < NT / 32; ++grp) {
                 const int r0 = grp * 32;
                 if (r0 >= nrec) break;
                 bool hit = false;
@@ -372,35 +374,34 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fwd_gauss(
         atomicAdd(&hdr->needed, (unsigned long long)(open ? (rg.y - rg.x) : s_maxstop));
 }
 
-template <int C, bool BF16>
+template <int TS, int C, bool BF16>
 cudaError_t launch_fwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     const unsigned grid = (unsigned)vt.tiles_total;
     if (vt.mode == 0) {
-        constexpr size_t smem = bilinear_fwd_smem<C, BF16>();
+        constexpr size_t smem = bilinear_fwd_smem<TS, C, BF16>();
         static bool set = false;
         if (!set) {
-            cudaError_t e = cudaFuncSetAttribute(k_blend_fwd_bilinear<C, BF16>,
+            cudaError_t e = cudaFuncSetAttribute(k_blend_fwd_bilinear<TS, C, BF16>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             set = true;
         }
         ProfScope ps("blend_fwd", s);
-        k_blend_fwd_bilinear<C, BF16><<<grid, kBlendThreads, smem, s>>>(vt, b.ranges, b.order, pts, b.rec,
-                                                                        b.t_final, b.last, b.hdr, b.trace);
+        k_blend_fwd_bilinear<TS, C, BF16><<<grid, TS * TS, smem, s>>>(vt, b.ranges, b.order, pts, b.rec,
+                                                                  b.t_final, b.last, b.hdr, b.trace);
         return cudaGetLastError();
     }
     ProfScope ps("blend_fwd", s);
-    if (false)
-        ;
-    else
-        k_blend_fwd_gauss<C, BF16><<<grid, kBlendThreads, 0, s>>>(vt, b.ranges, b.order, pts, b.rec,
-                                                                  b.t_final, b.last, b.hdr);
+    k_blend_fwd_gauss<TS, C, BF16><<<grid, TS * TS, 0, s>>>(vt, b.ranges, b.order, pts, b.rec, b.t_final,
+                                                        b.last, b.hdr);
     return cudaGetLastError();
 }
 
 template <int C>
 cudaError_t launch_fwd_c(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
-    return vt.bf16 ? launch_fwd_t<C, true>(vt, b, pts, s) : launch_fwd_t<C, false>(vt, b, pts, s);
+    if (vt.tile == 8)
+        return vt.bf16 ? launch_fwd_t<8, C, true>(vt, b, pts, s) : launch_fwd_t<8, C, false>(vt, b, pts, s);
+    return vt.bf16 ? launch_fwd_t<16, C, true>(vt, b, pts, s) : launch_fwd_t<16, C, false>(vt, b, pts, s);
 }
 
 }  // namespace

@@ -11,10 +11,8 @@
 namespace rast {
 
 constexpr int kMaxViews = 16;
-constexpr int kTile = 16;            // tile edge (pixels)
-constexpr int kTilePix = kTile * kTile;
-constexpr int kBlendThreads = 256;   // one thread per pixel of a 16x16 tile
-constexpr int kBatch = 256;          // records staged per blend batch
+constexpr int kTileDefault = 16;     // tile edge (pixels); 8 is the other compiled size
+constexpr int kTileMax = 16;
 
 // Status bits in the workspace header's error word.
 constexpr uint32_t kErrCapacity = 1u;
@@ -55,6 +53,7 @@ struct ViewTable {
     int32_t bf16;        // features stored as bf16
     int32_t mode;        // 0 bilinear, 1 Gaussian
     int32_t gauss_cov;   // 0 EWA, 1 isotropic screen
+    int32_t tile;        // tile edge in pixels (8 or 16)
     int32_t rec_words;   // record stride in 32-bit words (multiple of 4)
     int32_t feat_word;   // first feature word in a record
     float t_min, alpha_max, dilation;

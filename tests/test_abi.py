@@ -107,6 +107,11 @@ def test_workspace_size_and_layout(lib):
     lay = {e.name.decode(): (e.offset, e.bytes) for e in ents}
     assert lay["records"][1] == 1000 * 16 * 4
     assert lay["sorted_keys"][1] == 16 * 1000 * 4
+    # 8x8 tiles: ceil(100/8) x ceil(60/8) tile ranges
+    o8 = _opts(lib, tile=8)
+    n = lib.rasterize_workspace_layout(arr, 1, ct.byref(o8), ents, len(ents))
+    lay = {e.name.decode(): (e.offset, e.bytes) for e in ents}
+    assert lay["ranges"][1] == 13 * 8 * 8
 
 
 def test_argument_validation_is_synchronous(lib):
@@ -118,7 +123,9 @@ def test_argument_validation_is_synchronous(lib):
     assert B(arr, 0, 1, ct.byref(o), ws, big, None) == rast.RAST_ERR_ARG
     assert B(arr, 17, 1, ct.byref(o), ws, big, None) == rast.RAST_ERR_ARG
     assert B(arr, 1, 0, ct.byref(o), ws, big, None) == rast.RAST_ERR_ARG
-    assert B(arr, 1, 1, ct.byref(_opts(lib, tile=8)), ws, big, None) == rast.RAST_ERR_NOT_SUPPORTED
+    assert B(arr, 1, 1, ct.byref(_opts(lib, tile=32)), ws, big, None) == rast.RAST_ERR_NOT_SUPPORTED
+    assert B(arr, 1, 1, ct.byref(_opts(lib, tile=8, blend_depth=256)), ws, big, None) == \
+        rast.RAST_ERR_NOT_SUPPORTED
     assert B(arr, 1, 1, ct.byref(_opts(lib, mode=7)), ws, big, None) == rast.RAST_ERR_ARG
     assert B(arr, 1, 1, ct.byref(_opts(lib, alpha_max=1.0)), ws, big, None) == rast.RAST_ERR_ARG
     assert B(arr, 1, 1, ct.byref(o), None, big, None) == rast.RAST_ERR_ARG
