@@ -158,7 +158,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     pl.blk_cap = (npt + kScanItems - 1) / kScanItems + 1;
     pl.planA = make_sort_plan(bit_length(max_cull));
     pl.planC = make_sort_plan(bit_length((uint64_t)(ntile > 0 ? ntile - 1 : 0)));
-    pl.partial_floats = o->mode == RAST_SPLAT_BILINEAR ? C + 1 : C + 7;
+    pl.partial_floats = partial_stride(o->mode == RAST_SPLAT_BILINEAR ? C + 1 : C + 7);
 
     const int64_t N = npt, D = pl.copy_cap;
     pl.bytes[S_HDR] = sizeof(WsHeader);

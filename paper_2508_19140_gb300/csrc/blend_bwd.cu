@@ -42,7 +42,6 @@ constexpr int kStages = 3;  // cp.async ring depth (batches in flight per CTA)
 template <int TS, int C, bool BF16>
 constexpr size_t bilinear_bwd_smem() {
     return sizeof(uint32_t) * kStages * TS * TS * RecLayout<0, C, BF16>::words  // record ring
-           + sizeof(uint32_t) * kStages * TS * TS                              // slot-base ring
            + sizeof(float) * 4 * 2 * TS * TS                                   // (T a, w dL/da) per slot
            + sizeof(float) * TS * TS * C                                       // upstream dL/dF per pixel
            + 128;
@@ -60,12 +59,12 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
     const unsigned long long t_start = global_ns();
     const long long c_start = clock64();
     constexpr int P = C + 1;  // dfeat[C], dopacity
+    constexpr int PS = partial_stride(P);
     constexpr int RW = RecLayout<0, C, BF16>::words;
     constexpr int FW = RecLayout<0, C, BF16>::feat_word;
     extern __shared__ __align__(128) uint32_t s_dyn[];
     uint32_t* const s_ring = align128(s_dyn);                        // [kStages][NT][RW]
-    uint32_t* const s_base = s_ring + kStages * NT * RW;         // [kStages][NT]
-    float* const s_ta = reinterpret_cast<float*>(s_base + kStages * NT);  // [4][NT]
+    float* const s_ta = reinterpret_cast<float*>(s_ring + kStages * NT * RW);  // [4][NT]
     float* const s_da = s_ta + 4 * NT;                           // [4][NT]
     float* const s_gF = s_da + 4 * NT;                           // [NT][C]
     __shared__ uint32_t s_mask[NT][MW + 1];
@@ -120,8 +119,8 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
     const uint32_t end = rg.x + maxlast;
     const uint32_t nb = (maxlast - 1) / NT + 1;  // batches, processed last to first
 
-    // Iteration j handles batch nb-1-j. Thread t copies record t of each batch
-    // (and its slot base); idx[k] = point of iteration j + kStages + k.
+    // Iteration j handles batch nb-1-j. Thread t copies record t of each batch;
+    // idx[k] = point of iteration j + kStages + k.
     auto point_of = [&](uint32_t j) -> uint32_t {
         if (j >= nb) return 0xffffffffu;
         const uint32_t q = rg.x + (nb - 1 - j) * NT + tid;
@@ -134,7 +133,6 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
             const uint32_t* src = rec + (size_t)gi * RW;
 #pragma unroll
             for (int k = 0; k < RW; k += 4) cp_async16(dst + k, src + k);
-            cp_async4(s_base + st * NT + tid, base + gi);
         }
         cp_async_commit();
     };
@@ -163,6 +161,9 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
         }
         cp_async_wait<kStages - 1>();
         int slot_base = 0, X0 = 0, Y0 = 0;
+        bool single = false;   // the point has this one copy: its gradient is final here
+        uint32_t my_base = 0;  // first partial slot of a point with several copies
+        uint32_t gi_rec = 0;   // the record's point index
         if (have) {
             const uint4 g = *reinterpret_cast<const uint4*>(ring + tid * RW);
             const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
@@ -193,15 +194,17 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
             }
             // The point's tile rect (as the projection computed it) and this tile's rank in it.
             const int tx0 = max(bg.i0, 0) / TS, tx1 = min(bg.i0 + 1, V.W - 1) / TS;
-            const int ty0 = max(bg.j0, 0) / TS;
+            const int ty0 = max(bg.j0, 0) / TS, ty1 = min(bg.j0 + 1, V.H - 1) / TS;
             slot_base = (ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0);
-            if (q + 1 == end) {
-                uint32_t gi_last = gi_cur[0];
+            single = tx0 == tx1 && ty0 == ty1;
+            gi_rec = gi_cur[0];
 #pragma unroll
-                for (int k = 1; k < kStages; ++k)
-                    if (st == k) gi_last = gi_cur[k];
-                cutoff[tile] = make_uint2(g.z, gi_last);
-            }
+            for (int k = 1; k < kStages; ++k)
+                if (st == k) gi_rec = gi_cur[k];
+            // Only points with several copies need a partial slot; the load is
+            // consumed after the compositing loop, which hides its latency.
+            if (!single) my_base = base[gi_rec];
+            if (q + 1 == end) cutoff[tile] = make_uint2(g.z, gi_rec);
         }
         __syncthreads();
         if (inside && last > rel0) {
@@ -241,7 +244,6 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
         }
 #pragma unroll
         for (int w = 0; w < MW; ++w) s_mask[tid][w] = 0;
-        const uint32_t my_base = s_base[st * NT + tid];  // read before the slot is refilled
         __syncthreads();
         // Slot st is free (every pixel is done with it): refill it with iteration j + kStages.
         issue(j + kStages, idx[0]);
@@ -267,9 +269,17 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
                 }
                 acc[C] += s_da[sl * NT + tid];
             }
-            float* out = partial + (size_t)(my_base + (uint32_t)slot_base) * P;
+            if (single) {
+                // Sole copy: write the point's gradients (K8 leaves them alone).
+                const int64_t i = (int64_t)gi_rec - V.pt_off;
+                if (V.d_feat) store_row<C>(V.d_feat + i * C, acc);
+                if (V.d_opacity) V.d_opacity[i] = acc[C];
+            } else {
+                float row[PS];
 #pragma unroll
-            for (int k = 0; k < P; ++k) out[k] = acc[k];
+                for (int k = 0; k < PS; ++k) row[k] = k < P ? acc[k] : 0.f;
+                store_row<PS>(partial + (size_t)(my_base + (uint32_t)slot_base) * PS, row);
+            }
         }
         // No third barrier: the next iteration's writes to shared memory (this
         // thread's own contribution columns, the staging arrays and mask bits)
@@ -473,14 +483,18 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
         }
         __syncthreads();
         if (have) {
-            float* out = partial + (size_t)(my_bs + (uint32_t)slot) * P;
+            constexpr int PS = partial_stride(P);
+            float row[PS];
 #pragma unroll
-            for (int k = 0; k < P; ++k) {
+            for (int k = 0; k < PS; ++k) {
                 float acc = 0.f;
+                if (k < P) {
 #pragma unroll
-                for (int w = 0; w < NW; ++w) acc += s_contrib[(w * P + k) * kGBatch + tid];
-                out[k] = acc;
+                    for (int w = 0; w < NW; ++w) acc += s_contrib[(w * P + k) * kGBatch + tid];
+                }
+                row[k] = acc;
             }
+            store_row<PS>(partial + (size_t)(my_bs + (uint32_t)slot) * PS, row);
         }
         __syncthreads();
     }
@@ -495,6 +509,7 @@ __global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const 
                                                       const uint2* __restrict__ cutoff,
                                                       const float* __restrict__ partial) {
     constexpr int P = MODE == 0 ? C + 1 : C + 7;
+    constexpr int PS = partial_stride(P);
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= vt.n_total) return;
     const ViewDev& V = vt.v[view_of_point(vt, gi)];
@@ -504,25 +519,36 @@ __global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const 
     for (int k = 0; k < P; ++k) acc[k] = 0.f;
     const uint2 rc = rect[gi];
     const uint32_t cnt = rect_count(rc);
+    bool written = false;  // bilinear: the blend wrote the sole copy's gradients itself
     if (cnt) {
         const uint32_t zb = zbits[gi];
         const int tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff, ty1 = rc.y >> 16;
-        const float* pp = partial + (size_t)base[gi] * P;
+        const float* pp = partial + (size_t)base[gi] * PS;
         int k = 0;
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx, ++k) {
                 const uint2 co = cutoff[V.tile_off + (int64_t)ty * V.tiles_x + tx];
                 const bool done = zb < co.x || (zb == co.x && (uint32_t)gi <= co.y);
                 if (!done) continue;
+                if (MODE == 0 && cnt == 1) {
+                    written = true;
+                    continue;
+                }
+                const float4* row = reinterpret_cast<const float4*>(pp + (size_t)k * PS);
 #pragma unroll
-                for (int j = 0; j < P; ++j) acc[j] += pp[(size_t)k * P + j];
+                for (int j = 0; j < PS / 4; ++j) {
+                    const float4 x = row[j];
+                    if (4 * j + 0 < P) acc[4 * j + 0] += x.x;
+                    if (4 * j + 1 < P) acc[4 * j + 1] += x.y;
+                    if (4 * j + 2 < P) acc[4 * j + 2] += x.z;
+                    if (4 * j + 3 < P) acc[4 * j + 3] += x.w;
+                }
             }
     }
-    if (V.d_feat) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) V.d_feat[i * C + c] = acc[c];
+    if (!written) {
+        if (V.d_feat) store_row<C>(V.d_feat + i * C, acc);
+        if (V.d_opacity) V.d_opacity[i] = acc[C];
     }
-    if (V.d_opacity) V.d_opacity[i] = acc[C];
     if (MODE == 0) {
         if (V.d_xyz) {
             V.d_xyz[3 * i] = 0.f;

@@ -124,6 +124,22 @@ __device__ __forceinline__ uint32_t* align128(uint32_t* p) {
     return reinterpret_cast<uint32_t*>(a + ((128u - (sa & 127u)) & 127u));
 }
 
+// Stores N floats at dst: 16-byte vector stores when N is a multiple of 4 and
+// dst is 16-byte aligned, scalar stores otherwise.
+template <int N>
+__device__ __forceinline__ void store_row(float* dst, const float* v) {
+    if constexpr (N % 4 == 0) {
+        if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+#pragma unroll
+            for (int k = 0; k < N; k += 4)
+                *reinterpret_cast<float4*>(dst + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) dst[k] = v[k];
+}
+
 // Features of one record as FP32 registers.
 template <int C, bool BF16>
 __device__ __forceinline__ void load_features(const uint32_t* __restrict__ rp, float (&f)[C]) {

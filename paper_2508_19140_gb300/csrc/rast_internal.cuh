@@ -124,6 +124,10 @@ __device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w &
 
 // Packed tile rect of a point: (tx0 | ty0 << 16, tx1 | ty1 << 16), inclusive;
 // an empty rect is (1, 0) (tx0 > tx1).
+// Row stride (floats) of the per-copy gradient partials: P rounded up to a
+// multiple of 4 so every row is written and read as 16-byte vectors.
+__host__ __device__ constexpr int partial_stride(int P) { return (P + 3) & ~3; }
+
 __device__ __forceinline__ uint32_t rect_count(uint2 r) {
     const int tx0 = r.x & 0xffff, ty0 = r.x >> 16, tx1 = r.y & 0xffff, ty1 = r.y >> 16;
     if (tx1 < tx0 || ty1 < ty0) return 0;

@@ -16,13 +16,13 @@
 //                 holding the same digit; warps counted in ascending order),
 //                 publish the tile's per-digit counts, and add the counts of
 //                 all earlier tiles by looking back over their published words
-//                 (a tile whose whole prefix is known publishes it, so walks are
-//                 short). Keys are then staged in shared memory in digit order
-//                 and written out in runs.
+//                 eight at a time (a tile whose whole prefix is known publishes
+//                 it, so walks are short). Keys are then staged in shared
+//                 memory in digit order and written out in runs.
 // A tile only waits on tiles that running CTAs took before it, so the waits
 // always end; each wait is still bounded, and on expiry the kernel raises the
-// timeout bit of the workspace error word and carries on with a zero prefix
-// instead of spinning on. The element count may live on the device (copies
+// timeout bit of the workspace error word and carries on with the partial
+// prefix instead of spinning on. The element count may live on the device (copies
 // are counted on the GPU): launch shapes depend only on the capacity.
 #include <cuda/atomic>
 
@@ -38,6 +38,7 @@ constexpr int kWarpItems = 32 * kIPT;       // 512 keys per warp
 constexpr uint32_t kFlagAgg = 1u << 30;     // tile count published
 constexpr uint32_t kFlagPrefix = 2u << 30;  // inclusive prefix over tiles 0..t published
 constexpr uint32_t kValueMask = (1u << 30) - 1;
+constexpr int kLookback = 8;                // predecessor tiles read per look-back step
 
 int num_sms() {
     static int n = 0;
@@ -237,22 +238,42 @@ __global__ void __launch_bounds__(kThreads) k_sweep(
         for (int q = 0; q < VPT; ++q) {
             const int bin = threadIdx.x * VPT + q;
             if (bin >= BINS) continue;
+            // Look back over windows of kLookback predecessors: the window's
+            // loads are independent and in flight together, so a walk over
+            // many tiles that only published their own counts costs one load
+            // latency per window instead of one per tile.
             uint32_t excl = 0;
-            for (int64_t t = tile - 1; t >= 0; --t) {
-                cuda::atomic_ref<uint32_t, cuda::thread_scope_device> w(status[t * BINS + bin]);
-                uint32_t val = w.load(cuda::memory_order_relaxed);
-                uint32_t spins = 0;
-                while ((val >> 30) == 0u) {
+            int64_t t = tile - 1;
+            uint32_t spins = 0;
+            while (t >= 0) {
+                uint32_t w[kLookback];
+#pragma unroll
+                for (int j = 0; j < kLookback; ++j) {
+                    w[j] = kFlagPrefix;  // before tile 0: an empty prefix
+                    if (t - j >= 0) {
+                        cuda::atomic_ref<uint32_t, cuda::thread_scope_device> a(status[(t - j) * BINS + bin]);
+                        w[j] = a.load(cuda::memory_order_relaxed);
+                    }
+                }
+                int j = 0;
+                bool found = false;
+                for (; j < kLookback; ++j) {
+                    if ((w[j] >> 30) == 0u) break;  // not published yet: poll again from here
+                    excl += w[j] & kValueMask;
+                    if ((w[j] & kFlagPrefix) != 0u) {
+                        found = true;
+                        break;
+                    }
+                }
+                if (found) break;
+                t -= j;
+                if (j < kLookback) {
                     if (++spins > (1u << 22)) {  // a predecessor never published: give up
                         atomicOr(err, kErrTimeout);
-                        val = kFlagPrefix;
                         break;
                     }
                     __nanosleep(64);
-                    val = w.load(cuda::memory_order_relaxed);
                 }
-                excl += val & kValueMask;
-                if ((val & kFlagPrefix) != 0u) break;
             }
             if (tile != 0) {
                 cuda::atomic_ref<uint32_t, cuda::thread_scope_device> w(my[bin]);
