@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--config", type=int, default=2, help="workload id (2: 4M points, 1280x832)")
     ap.add_argument("--scale-points", type=float, default=1.0, help="shrink the point count (tests)")
     ap.add_argument("--tile", type=int, default=16, help="tile edge: 16, 8, or 0 = autotuned")
+    ap.add_argument("--blend-depth", type=int, default=0, help="records per blend batch (0 = tile^2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
@@ -250,7 +251,7 @@ def run_ours(args, ws_, rank, local):
                               scale_points=args.scale_points)
     bf16 = scene.feat_dtype == "bf16"
     gauss = scene.mode == "gaussian"
-    opts = rast.make_opts(mode=scene.mode, tile=args.tile or 16)
+    opts = rast.make_opts(mode=scene.mode, tile=args.tile or 16, blend_depth=args.blend_depth)
     tens, cviews = make_views(scene, dev, bf16)
     ws_bytes = rast.rasterize_workspace_size(cviews, opts)
     wsp = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
@@ -394,7 +395,8 @@ def run_ours(args, ws_, rank, local):
         "dtype": "bf16-features/f32" if bf16 else "f32", "data": "synthetic",
         "config": {"workload": scene.name, "config_id": scene.config_id, "n_points_per_gpu": n_points,
                    "views": len(scene.views), "width": v0.camera.width, "height": v0.camera.height,
-                   "channels": C, "mode": scene.mode, "tile": int(opts.tile), "pass": "fwd+bwd" if do_bwd else "fwd",
+                   "channels": C, "mode": scene.mode, "tile": int(opts.tile),
+                   "blend_depth": int(opts.blend_depth) or int(opts.tile) ** 2, "pass": "fwd+bwd" if do_bwd else "fwd",
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
                    "parallelism": f"independent frame per GPU x{ws_}"},
         "fwd_points_per_s": round(n_points * ws_ / (fwd_ms / 1e3), 1) if fwd_ms else None,

@@ -83,8 +83,9 @@ typedef struct {
     int32_t gauss_cov;     /* rast_gauss_cov_t */
     int32_t tile;          /* tile edge in pixels: 16 (default) or 8; the images and gradients
                               do not depend on it, only the work split does */
-    int32_t blend_depth;   /* records staged per blend batch: 0 = default (tile * tile, the
-                              only compiled value) */
+    int32_t blend_depth;   /* records staged per blend batch: 0 = tile * tile (default);
+                              bilinear also 2 * tile * tile, and 4 * tile * tile for 8x8
+                              tiles; Gaussian tile * tile only. Results do not depend on it */
     float t_min;           /* early termination: stop before T (1 - a) < t_min (1e-4) */
     float alpha_max;       /* alpha clamp (0.99) */
     float dilation;        /* screen-space dilation variance, Gaussian mode (0.16) */

@@ -71,13 +71,23 @@ rast_status_t check_view(const rast_view_t& v, int pass, int T) {
     return RAST_OK;
 }
 
+// Compiled blend depths (records per blend batch): bilinear tile^2 x {1, 2},
+// and x 4 for 8x8 tiles; Gaussian tile^2.
+bool blend_depth_supported(int mode, int tile, int depth) {
+    const int nt = tile * tile;
+    if (depth == nt) return true;
+    if (mode != RAST_SPLAT_BILINEAR) return false;
+    return depth == 2 * nt || (tile == 8 && depth == 4 * nt);
+}
+
 rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_opts_t* o, int pass,
                         Plan& pl) {
     if (!views || !o || n_views < 1 || n_views > kMaxViews) return RAST_ERR_ARG;
     if (o->mode != RAST_SPLAT_BILINEAR && o->mode != RAST_SPLAT_GAUSSIAN) return RAST_ERR_ARG;
     if (o->gauss_cov != RAST_GAUSS_EWA && o->gauss_cov != RAST_GAUSS_ISO_SCREEN) return RAST_ERR_ARG;
     if (o->tile != 8 && o->tile != 16) return RAST_ERR_NOT_SUPPORTED;
-    if (o->blend_depth != 0 && o->blend_depth != o->tile * o->tile) return RAST_ERR_NOT_SUPPORTED;
+    const int depth = o->blend_depth == 0 ? o->tile * o->tile : o->blend_depth;
+    if (!blend_depth_supported(o->mode, o->tile, depth)) return RAST_ERR_NOT_SUPPORTED;
     if (!(o->t_min >= 0.f) || !(o->alpha_max > 0.f && o->alpha_max < 1.f)) return RAST_ERR_ARG;
     if (!(o->dilation >= 0.f) || o->max_copies < 0) return RAST_ERR_ARG;
     const int C = views[0].pts.channels;
@@ -93,6 +103,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     vt.mode = o->mode;
     vt.gauss_cov = o->gauss_cov;
     vt.tile = o->tile;
+    vt.blend_depth = depth;
     vt.t_min = o->t_min;
     vt.alpha_max = o->alpha_max;
     vt.dilation = o->dilation;

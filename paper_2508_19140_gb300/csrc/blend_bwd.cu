@@ -37,25 +37,32 @@ __device__ __forceinline__ uint32_t block_max_u32(uint32_t x, uint32_t* s) {
 
 // ---------------------------------------------------------------- bilinear
 
-constexpr int kStages = 3;  // cp.async ring depth (batches in flight per CTA)
+// cp.async ring depth (batches in flight per CTA): three batches of one record
+// per thread, two of deeper batches.
+template <int RPT>
+constexpr int stages_for() { return RPT == 1 ? 3 : 2; }
 
-template <int TS, int C, bool BF16>
+template <int TS, int RPT, int C, bool BF16>
 constexpr size_t bilinear_bwd_smem() {
-    return sizeof(uint32_t) * kStages * TS * TS * RecLayout<0, C, BF16>::words  // record ring
-           + sizeof(float) * 4 * 2 * TS * TS                                   // (T a, w dL/da) per slot
-           + sizeof(float) * TS * TS * C                                       // upstream dL/dF per pixel
+    constexpr int D = TS * TS * RPT;
+    return sizeof(uint32_t) * stages_for<RPT>() * D * RecLayout<0, C, BF16>::words  // record ring
+           + sizeof(float) * 4 * 2 * D                                              // (T a, w dL/da) per slot
+           + sizeof(float) * TS * TS * C                                            // upstream dL/dF per pixel
            + 128;
 }
 
-template <int TS, int C, bool BF16>
+// RPT = records each thread stages per batch (blend depth D = TS * TS * RPT).
+template <int TS, int RPT, int C, bool BF16>
 __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec,
     const float* __restrict__ t_final, const uint32_t* __restrict__ last_in,
     const uint32_t* __restrict__ base, float* __restrict__ partial, uint2* __restrict__ cutoff,
     WsHeader* __restrict__ hdr, unsigned long long* __restrict__ trace) {
-    constexpr int NT = TS * TS;    // threads = pixels = records per batch
-    constexpr int MW = NT / 32;  // mask words per pixel
+    constexpr int NT = TS * TS;  // threads = pixels
+    constexpr int D = NT * RPT;  // records per batch
+    constexpr int MW = D / 32;   // mask words per pixel
+    constexpr int kStages = stages_for<RPT>();
     const unsigned long long t_start = global_ns();
     const long long c_start = clock64();
     constexpr int P = C + 1;  // dfeat[C], dopacity
@@ -63,22 +70,22 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
     constexpr int RW = RecLayout<0, C, BF16>::words;
     constexpr int FW = RecLayout<0, C, BF16>::feat_word;
     extern __shared__ __align__(128) uint32_t s_dyn[];
-    uint32_t* const s_ring = align128(s_dyn);                        // [kStages][NT][RW]
-    float* const s_ta = reinterpret_cast<float*>(s_ring + kStages * NT * RW);  // [4][NT]
-    float* const s_da = s_ta + 4 * NT;                           // [4][NT]
-    float* const s_gF = s_da + 4 * NT;                           // [NT][C]
+    uint32_t* const s_ring = align128(s_dyn);                                 // [kStages][D][RW]
+    float* const s_ta = reinterpret_cast<float*>(s_ring + kStages * D * RW);  // [4][D]
+    float* const s_da = s_ta + 4 * D;                                         // [4][D]
+    float* const s_gF = s_da + 4 * D;                                         // [NT][C]
     __shared__ uint32_t s_mask[NT][MW + 1];
-    __shared__ float s_w[4][NT];    // bilinear weight per slot
-    __shared__ float s_inv[4][NT];  // 1 / (1 - alpha) per slot
-    __shared__ float s_o[NT];       // opacity per record
-    __shared__ uint32_t s_anchor[NT];
+    __shared__ float s_w[4][D];    // bilinear weight per slot
+    __shared__ float s_inv[4][D];  // 1 / (1 - alpha) per slot
+    __shared__ float s_o[D];       // opacity per record
+    __shared__ uint32_t s_anchor[D];
     __shared__ uint32_t s_red;
 
     const int64_t tile = order[blockIdx.x];
     const ViewDev& V = vt.v[view_of_tile(vt, tile)];
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int lx = tid & (TS - 1), ly = tid / TS;
     const int px = tx * TS + lx, py = ty * TS + ly;
     const bool inside = px < V.W && py < V.H;
@@ -117,71 +124,88 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
     float Sg = 0.f, SD = 0.f;
     const float Kd = -gA * Tfin;  // constant part of the 1/(1-a) term
     const uint32_t end = rg.x + maxlast;
-    const uint32_t nb = (maxlast - 1) / NT + 1;  // batches, processed last to first
+    const uint32_t nb = (maxlast - 1) / D + 1;  // batches, processed last to first
 
-    // Iteration j handles batch nb-1-j. Thread t copies record t of each batch;
-    // idx[k] = point of iteration j + kStages + k.
-    auto point_of = [&](uint32_t j) -> uint32_t {
+    // Iteration j handles batch nb-1-j. Thread t copies records t, t + NT, ...
+    // of each batch; idx[s] = points of iteration j + kStages + s.
+    auto point_of = [&](uint32_t j, int k) -> uint32_t {
         if (j >= nb) return 0xffffffffu;
-        const uint32_t q = rg.x + (nb - 1 - j) * NT + tid;
+        const uint32_t q = rg.x + (nb - 1 - j) * D + k * NT + tid;
         return q < end ? pts[q] : 0xffffffffu;
     };
-    auto issue = [&](uint32_t j, uint32_t gi) {
-        if (gi != 0xffffffffu) {
-            const int st = (int)(j % kStages);
-            uint32_t* dst = s_ring + ((size_t)st * NT + tid) * RW;
-            const uint32_t* src = rec + (size_t)gi * RW;
+    auto issue = [&](uint32_t j, const uint32_t (&gi)[RPT]) {
+        const int st = (int)(j % kStages);
 #pragma unroll
-            for (int k = 0; k < RW; k += 4) cp_async16(dst + k, src + k);
+        for (int k = 0; k < RPT; ++k) {
+            if (gi[k] != 0xffffffffu) {
+                uint32_t* dst = s_ring + ((size_t)st * D + k * NT + tid) * RW;
+                const uint32_t* src = rec + (size_t)gi[k] * RW;
+#pragma unroll
+                for (int q = 0; q < RW; q += 4) cp_async16(dst + q, src + q);
+            }
         }
         cp_async_commit();
     };
-    uint32_t idx[kStages];
-    uint32_t gi_cur[kStages];  // point index per ring slot (for the cutoff record)
+    uint32_t idx[kStages][RPT];
+    uint32_t gi_cur[kStages][RPT];  // point indices per ring slot
 #pragma unroll
-    for (int k = 0; k < kStages; ++k) idx[k] = point_of(k);
+    for (int st = 0; st < kStages; ++st)
 #pragma unroll
-    for (int k = 0; k < kStages; ++k) {
-        issue(k, idx[k]);
-        gi_cur[k] = idx[k];
-        idx[k] = point_of(k + kStages);
+        for (int k = 0; k < RPT; ++k) idx[st][k] = point_of(st, k);
+#pragma unroll
+    for (int st = 0; st < kStages; ++st) {
+        issue(st, idx[st]);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            gi_cur[st][k] = idx[st][k];
+            idx[st][k] = point_of(st + kStages, k);
+        }
     }
 
     for (uint32_t j = 0; j < nb; ++j) {
         const uint32_t bi = nb - 1 - j;
         const int st = (int)(j % kStages);
-        const uint32_t* ring = s_ring + (size_t)st * NT * RW;
-        const uint32_t rel0 = bi * NT;
-        const uint32_t q = rg.x + rel0 + tid;
-        const bool have = q < end;
+        const uint32_t* ring = s_ring + (size_t)st * D * RW;
+        const uint32_t rel0 = bi * D;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 4 * RPT; ++k) {
             s_ta[k * NT + tid] = 0.f;
             s_da[k * NT + tid] = 0.f;
         }
         cp_async_wait<kStages - 1>();
-        int slot_base = 0, X0 = 0, Y0 = 0;
-        bool single = false;   // the point has this one copy: its gradient is final here
-        uint32_t my_base = 0;  // first partial slot of a point with several copies
-        uint32_t gi_rec = 0;   // the record's point index
-        if (have) {
-            const uint4 g = *reinterpret_cast<const uint4*>(ring + tid * RW);
+        // Per staged record: slot rank, anchor, and where its gradient goes.
+        int slot_base[RPT], anchor[RPT];
+        bool single[RPT];      // the point has this one copy: its gradient is final here
+        uint32_t my_base[RPT]; // first partial slot of a point with several copies
+        uint32_t gi_rec[RPT];  // the record's point index
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            slot_base[k] = 0;
+            anchor[k] = 0;
+            single[k] = false;
+            my_base[k] = 0;
+            gi_rec[k] = 0xffffffffu;
+            const int r = k * NT + tid;
+            const uint32_t q = rg.x + rel0 + r;
+            if (q >= end) continue;
+            const uint4 g = *reinterpret_cast<const uint4*>(ring + r * RW);
             const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
             const float o = __uint_as_float(g.w);
             const float ax = __fsub_rn(1.f, bg.a), by = __fsub_rn(1.f, bg.b);
             const float w0 = __fmul_rn(ax, by), w1 = __fmul_rn(bg.a, by);
             const float w2 = __fmul_rn(ax, bg.b), w3 = __fmul_rn(bg.a, bg.b);
-            s_w[0][tid] = w0; s_w[1][tid] = w1; s_w[2][tid] = w2; s_w[3][tid] = w3;
-            s_o[tid] = o;
+            s_w[0][r] = w0; s_w[1][r] = w1; s_w[2][r] = w2; s_w[3][r] = w3;
+            s_o[r] = o;
             // 1 / (1 - alpha) of each slot, alpha = min(o w, amax) exactly as the forward has it
-            s_inv[0][tid] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w0), amax)));
-            s_inv[1][tid] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w1), amax)));
-            s_inv[2][tid] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w2), amax)));
-            s_inv[3][tid] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w3), amax)));
-            X0 = bg.i0 - tx * TS;
-            Y0 = bg.j0 - ty * TS;
-            s_anchor[tid] = (uint32_t)(X0 + 1) | ((uint32_t)(Y0 + 1) << 8);
+            s_inv[0][r] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w0), amax)));
+            s_inv[1][r] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w1), amax)));
+            s_inv[2][r] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w2), amax)));
+            s_inv[3][r] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w3), amax)));
+            const int X0 = bg.i0 - tx * TS, Y0 = bg.j0 - ty * TS;
+            anchor[k] = (X0 + 1) | ((Y0 + 1) << 8);
+            s_anchor[r] = (uint32_t)anchor[k];
             const uint32_t bit = 1u << lane;
+            const int word = r >> 5;
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
                 const int Y = Y0 + dy;
@@ -189,22 +213,23 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
 #pragma unroll
                 for (int dx = 0; dx < 2; ++dx) {
                     const int X = X0 + dx;
-                    if ((unsigned)X < (unsigned)TS) atomicOr(&s_mask[Y * TS + X][warp], bit);
+                    if ((unsigned)X < (unsigned)TS) atomicOr(&s_mask[Y * TS + X][word], bit);
                 }
             }
             // The point's tile rect (as the projection computed it) and this tile's rank in it.
             const int tx0 = max(bg.i0, 0) / TS, tx1 = min(bg.i0 + 1, V.W - 1) / TS;
             const int ty0 = max(bg.j0, 0) / TS, ty1 = min(bg.j0 + 1, V.H - 1) / TS;
-            slot_base = (ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0);
-            single = tx0 == tx1 && ty0 == ty1;
-            gi_rec = gi_cur[0];
+            slot_base[k] = (ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0);
+            single[k] = tx0 == tx1 && ty0 == ty1;
+            uint32_t gi = gi_cur[0][k];
 #pragma unroll
-            for (int k = 1; k < kStages; ++k)
-                if (st == k) gi_rec = gi_cur[k];
+            for (int s2 = 1; s2 < kStages; ++s2)
+                if (st == s2) gi = gi_cur[s2][k];
+            gi_rec[k] = gi;
             // Only points with several copies need a partial slot; the load is
             // consumed after the compositing loop, which hides its latency.
-            if (!single) my_base = base[gi_rec];
-            if (q + 1 == end) cutoff[tile] = make_uint2(g.z, gi_rec);
+            if (!single[k]) my_base[k] = base[gi];
+            if (q + 1 == end) cutoff[tile] = make_uint2(g.z, gi);
         }
         __syncthreads();
         if (inside && last > rel0) {
@@ -238,8 +263,8 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
                 Sg = fmaf(ta, fdot, Sg);
                 SD = fmaf(ta, z, SD);
                 T = Tk;
-                s_ta[slot * NT + r] = ta;
-                s_da[slot * NT + r] = (ow <= amax) ? wgt * dalpha : 0.f;
+                s_ta[slot * D + r] = ta;
+                s_da[slot * D + r] = (ow <= amax) ? wgt * dalpha : 0.f;
             }
         }
 #pragma unroll
@@ -248,37 +273,47 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
         // Slot st is free (every pixel is done with it): refill it with iteration j + kStages.
         issue(j + kStages, idx[0]);
 #pragma unroll
-        for (int k = 0; k < kStages; ++k)
-            if (st == k) gi_cur[k] = idx[0];
+        for (int s2 = 0; s2 < kStages; ++s2)
+            if (st == s2) {
 #pragma unroll
-        for (int k = 0; k + 1 < kStages; ++k) idx[k] = idx[k + 1];
-        idx[kStages - 1] = point_of(j + 2 * kStages);
-        if (have) {
+                for (int k = 0; k < RPT; ++k) gi_cur[s2][k] = idx[0][k];
+            }
+#pragma unroll
+        for (int s2 = 0; s2 + 1 < kStages; ++s2)
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) idx[s2][k] = idx[s2 + 1][k];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) idx[kStages - 1][k] = point_of(j + 2 * kStages, k);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (gi_rec[k] == 0xffffffffu) continue;
+            const int r = k * NT + tid;
+            const int X0 = (anchor[k] & 0xff) - 1, Y0 = (anchor[k] >> 8) - 1;
             // dL/df = sum over the 2x2 slots (fixed order) of T a times the pixel's dL/dF.
             float acc[P];
 #pragma unroll
-            for (int k = 0; k < P; ++k) acc[k] = 0.f;
+            for (int q = 0; q < P; ++q) acc[q] = 0.f;
 #pragma unroll
             for (int sl = 0; sl < 4; ++sl) {
                 const int X = X0 + (sl & 1), Y = Y0 + (sl >> 1);
-                const float ta = s_ta[sl * NT + tid];
+                const float ta = s_ta[sl * D + r];
                 if ((unsigned)X < (unsigned)TS && (unsigned)Y < (unsigned)TS) {
                     const float* gp = s_gF + (Y * TS + X) * C;
 #pragma unroll
                     for (int c = 0; c < C; ++c) acc[c] += ta * gp[c];
                 }
-                acc[C] += s_da[sl * NT + tid];
+                acc[C] += s_da[sl * D + r];
             }
-            if (single) {
+            if (single[k]) {
                 // Sole copy: write the point's gradients (K8 leaves them alone).
-                const int64_t i = (int64_t)gi_rec - V.pt_off;
+                const int64_t i = (int64_t)gi_rec[k] - V.pt_off;
                 if (V.d_feat) store_row<C>(V.d_feat + i * C, acc);
                 if (V.d_opacity) V.d_opacity[i] = acc[C];
             } else {
                 float row[PS];
 #pragma unroll
-                for (int k = 0; k < PS; ++k) row[k] = k < P ? acc[k] : 0.f;
-                store_row<PS>(partial + (size_t)(my_base + (uint32_t)slot_base) * PS, row);
+                for (int q = 0; q < PS; ++q) row[q] = q < P ? acc[q] : 0.f;
+                store_row<PS>(partial + (size_t)(my_base[k] + (uint32_t)slot_base[k]) * PS, row);
             }
         }
         // No third barrier: the next iteration's writes to shared memory (this
@@ -626,20 +661,20 @@ __global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const 
     if (V.d_scale) V.d_scale[i] = V.scale ? gs : 0.f;
 }
 
-template <int TS, int C, bool BF16>
+template <int TS, int RPT, int C, bool BF16>
 cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     const unsigned grid = (unsigned)vt.tiles_total;
     if (vt.mode == 0) {
-        constexpr size_t smem = bilinear_bwd_smem<TS, C, BF16>();
+        constexpr size_t smem = bilinear_bwd_smem<TS, RPT, C, BF16>();
         static bool set = false;
         if (!set) {
-            cudaError_t e = cudaFuncSetAttribute(k_blend_bwd_bilinear<TS, C, BF16>,
+            cudaError_t e = cudaFuncSetAttribute(k_blend_bwd_bilinear<TS, RPT, C, BF16>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             set = true;
         }
         ProfScope ps("blend_bwd", s);
-        k_blend_bwd_bilinear<TS, C, BF16><<<grid, TS * TS, smem, s>>>(
+        k_blend_bwd_bilinear<TS, RPT, C, BF16><<<grid, TS * TS, smem, s>>>(
             vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.cutoff, b.hdr,
             b.trace);
     } else {
@@ -660,11 +695,21 @@ cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts
     return cudaGetLastError();
 }
 
+template <int TS, int C, bool BF16>
+cudaError_t launch_bwd_d(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    const int rpt = vt.mode == 0 ? vt.blend_depth / (TS * TS) : 1;
+    if constexpr (TS == 8) {
+        if (rpt == 4) return launch_bwd_t<TS, 4, C, BF16>(vt, b, pts, s);
+    }
+    if (rpt == 2) return launch_bwd_t<TS, 2, C, BF16>(vt, b, pts, s);
+    return launch_bwd_t<TS, 1, C, BF16>(vt, b, pts, s);
+}
+
 template <int C>
 cudaError_t launch_bwd_c(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     if (vt.tile == 8)
-        return vt.bf16 ? launch_bwd_t<8, C, true>(vt, b, pts, s) : launch_bwd_t<8, C, false>(vt, b, pts, s);
-    return vt.bf16 ? launch_bwd_t<16, C, true>(vt, b, pts, s) : launch_bwd_t<16, C, false>(vt, b, pts, s);
+        return vt.bf16 ? launch_bwd_d<8, C, true>(vt, b, pts, s) : launch_bwd_d<8, C, false>(vt, b, pts, s);
+    return vt.bf16 ? launch_bwd_d<16, C, true>(vt, b, pts, s) : launch_bwd_d<16, C, false>(vt, b, pts, s);
 }
 
 template <int C>

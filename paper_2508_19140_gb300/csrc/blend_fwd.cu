@@ -65,29 +65,38 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ r
     }
 }
 
-constexpr int kStages = 3;  // cp.async ring depth (batches in flight per CTA)
+// cp.async ring depth (batches in flight per CTA): three batches of one record
+// per thread, two of deeper batches.
+template <int RPT>
+constexpr int stages_for() { return RPT == 1 ? 3 : 2; }
 
-template <int TS, int C, bool BF16>
+template <int TS, int RPT, int C, bool BF16>
 constexpr size_t bilinear_fwd_smem() {
-    return sizeof(uint32_t) * kStages * TS * TS * RecLayout<0, C, BF16>::words + 128;
+    return sizeof(uint32_t) * stages_for<RPT>() * TS * TS * RPT * RecLayout<0, C, BF16>::words + 128;
 }
 
-template <int TS, int C, bool BF16>
+// RPT = records each thread stages per batch: the batch ("blend depth") is
+// D = TS * TS * RPT records; every pixel composites the records of a batch
+// that cover it between two barriers, so a deeper batch spends fewer barriers
+// per record and evens out the pixels' per-batch fragment counts.
+template <int TS, int RPT, int C, bool BF16>
 __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec, float* __restrict__ t_final,
     uint32_t* __restrict__ last_out, WsHeader* __restrict__ hdr, unsigned long long* __restrict__ trace) {
-    constexpr int NT = TS * TS;       // threads = pixels = records per batch
-    constexpr int MW = NT / 32;     // mask words per pixel
+    constexpr int NT = TS * TS;     // threads = pixels
+    constexpr int D = NT * RPT;     // records per batch
+    constexpr int MW = D / 32;      // mask words per pixel
+    constexpr int kStages = stages_for<RPT>();
     const unsigned long long t_start = global_ns();
     const long long c_start = clock64();
     constexpr int RW = RecLayout<0, C, BF16>::words;
     constexpr int FW = RecLayout<0, C, BF16>::feat_word;
     extern __shared__ __align__(128) uint32_t s_dyn[];
-    uint32_t* const s_ring = align128(s_dyn);  // [kStages][NT][RW] raw records
+    uint32_t* const s_ring = align128(s_dyn);  // [kStages][D][RW] raw records
     __shared__ uint32_t s_mask[NT][MW + 1];    // MW words + 1 pad: conflict-free row reads
-    __shared__ float s_alpha[4][NT];       // alpha of each record's 2x2 slots (FP32, pinned ops)
-    __shared__ uint32_t s_anchor[NT];      // tile-local anchor (X0 + 1) | (Y0 + 1) << 8
+    __shared__ float s_alpha[4][D];            // alpha of each record's 2x2 slots (FP32, pinned ops)
+    __shared__ uint32_t s_anchor[D];           // tile-local anchor (X0 + 1) | (Y0 + 1) << 8
     __shared__ uint32_t s_maxstop;
 
     const int64_t tile = order[blockIdx.x];
@@ -100,7 +109,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     const bool inside = px < V.W && py < V.H;
     const uint2 rg = ranges[tile];
     const uint32_t len = rg.y - rg.x;
-    const uint32_t nbatch = (len + NT - 1) / NT;
+    const uint32_t nbatch = (len + D - 1) / D;
     const float amax = vt.alpha_max, tmin = vt.t_min;
 
     float T = 1.f, A = 0.f, Dp = 0.f;
@@ -113,63 +122,75 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     for (int w = 0; w < MW; ++w) s_mask[tid][w] = 0;
     if (tid == 0) s_maxstop = 0;
 
-    // Thread t copies record t of every batch. idx[k] = point index of batch
-    // (j + kStages + k) while batch j is processed (loaded kStages batches ahead).
-    auto point_of = [&](uint32_t j) -> uint32_t {
-        const uint32_t r = j * NT + tid;
+    // Thread t copies records t, t + NT, ... of every batch. idx[s] = point
+    // indices of batch j + kStages + s while batch j is processed (the copies
+    // are issued kStages batches ahead, the indices read kStages further).
+    auto point_of = [&](uint32_t j, int k) -> uint32_t {
+        const uint32_t r = j * D + k * NT + tid;
         return r < len ? pts[rg.x + r] : 0xffffffffu;
     };
-    auto issue = [&](uint32_t j, uint32_t gi) {
-        if (gi != 0xffffffffu) {
-            uint32_t* dst = s_ring + ((size_t)(j % kStages) * NT + tid) * RW;
-            const uint32_t* src = rec + (size_t)gi * RW;
+    auto issue = [&](uint32_t j, const uint32_t (&gi)[RPT]) {
 #pragma unroll
-            for (int k = 0; k < RW; k += 4) cp_async16(dst + k, src + k);
+        for (int k = 0; k < RPT; ++k) {
+            if (gi[k] != 0xffffffffu) {
+                uint32_t* dst = s_ring + ((size_t)(j % kStages) * D + k * NT + tid) * RW;
+                const uint32_t* src = rec + (size_t)gi[k] * RW;
+#pragma unroll
+                for (int q = 0; q < RW; q += 4) cp_async16(dst + q, src + q);
+            }
         }
         cp_async_commit();
     };
-    uint32_t idx[kStages];
+    uint32_t idx[kStages][RPT];
 #pragma unroll
-    for (int k = 0; k < kStages; ++k) idx[k] = point_of(k);
+    for (int st = 0; st < kStages; ++st)
 #pragma unroll
-    for (int k = 0; k < kStages; ++k) {
-        issue(k, idx[k]);
-        idx[k] = point_of(k + kStages);
+        for (int k = 0; k < RPT; ++k) idx[st][k] = point_of(st, k);
+#pragma unroll
+    for (int st = 0; st < kStages; ++st) {
+        issue(st, idx[st]);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) idx[st][k] = point_of(st + kStages, k);
     }
 
     for (uint32_t j = 0; j < nbatch; ++j) {
-        const uint32_t* ring = s_ring + (size_t)(j % kStages) * NT * RW;
-        cp_async_wait<kStages - 1>();  // this thread's copy of batch j has landed
-        const uint32_t rel0 = j * NT;
-        if (rel0 + tid < len) {
-            // Per record: the four fragment alphas of its 2x2 box (the ops of
-            // bilin_weight and the clamp, so every pixel sees the same FP32 bits)
-            // and one mask bit per covered pixel of this tile.
-            const uint4 g = *reinterpret_cast<const uint4*>(ring + tid * RW);
-            const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
-            const float o = __uint_as_float(g.w);
-            const float ax = __fsub_rn(1.f, bg.a), by = __fsub_rn(1.f, bg.b);
-            s_alpha[0][tid] = fminf(__fmul_rn(o, __fmul_rn(ax, by)), amax);
-            s_alpha[1][tid] = fminf(__fmul_rn(o, __fmul_rn(bg.a, by)), amax);
-            s_alpha[2][tid] = fminf(__fmul_rn(o, __fmul_rn(ax, bg.b)), amax);
-            s_alpha[3][tid] = fminf(__fmul_rn(o, __fmul_rn(bg.a, bg.b)), amax);
-            const int X0 = bg.i0 - tx * TS, Y0 = bg.j0 - ty * TS;
-            s_anchor[tid] = (uint32_t)(X0 + 1) | ((uint32_t)(Y0 + 1) << 8);
-            const uint32_t bit = 1u << lane;
+        const uint32_t* ring = s_ring + (size_t)(j % kStages) * D * RW;
+        cp_async_wait<kStages - 1>();  // this thread's copies of batch j have landed
+        const uint32_t rel0 = j * D;
 #pragma unroll
-            for (int dy = 0; dy < 2; ++dy) {
-                const int Y = Y0 + dy;
-                if ((unsigned)Y >= (unsigned)TS) continue;
+        for (int k = 0; k < RPT; ++k) {
+            const int r = k * NT + tid;
+            if (rel0 + r < len) {
+                // Per record: the four fragment alphas of its 2x2 box (the ops of
+                // bilin_weight and the clamp, so every pixel sees the same FP32
+                // bits) and one mask bit per covered pixel of this tile.
+                const uint4 g = *reinterpret_cast<const uint4*>(ring + r * RW);
+                const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
+                const float o = __uint_as_float(g.w);
+                const float ax = __fsub_rn(1.f, bg.a), by = __fsub_rn(1.f, bg.b);
+                s_alpha[0][r] = fminf(__fmul_rn(o, __fmul_rn(ax, by)), amax);
+                s_alpha[1][r] = fminf(__fmul_rn(o, __fmul_rn(bg.a, by)), amax);
+                s_alpha[2][r] = fminf(__fmul_rn(o, __fmul_rn(ax, bg.b)), amax);
+                s_alpha[3][r] = fminf(__fmul_rn(o, __fmul_rn(bg.a, bg.b)), amax);
+                const int X0 = bg.i0 - tx * TS, Y0 = bg.j0 - ty * TS;
+                s_anchor[r] = (uint32_t)(X0 + 1) | ((uint32_t)(Y0 + 1) << 8);
+                const uint32_t bit = 1u << lane;
+                const int word = r >> 5;
 #pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int X = X0 + dx;
-                    if ((unsigned)X < (unsigned)TS) atomicOr(&s_mask[Y * TS + X][warp], bit);
+                for (int dy = 0; dy < 2; ++dy) {
+                    const int Y = Y0 + dy;
+                    if ((unsigned)Y >= (unsigned)TS) continue;
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const int X = X0 + dx;
+                        if ((unsigned)X < (unsigned)TS) atomicOr(&s_mask[Y * TS + X][word], bit);
+                    }
                 }
             }
         }
         if (__syncthreads_count(!done) == 0) break;
         if (!done) {
-            // One loop over every set bit of the pixel's 256-bit mask, in order.
+            // One loop over every set bit of the pixel's D-bit mask, in order.
             int w = 0;
             uint32_t m = s_mask[tid][0];
 #pragma unroll 1
@@ -205,8 +226,11 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
         // Slot j % kStages is free: refill it with batch j + kStages.
         issue(j + kStages, idx[0]);
 #pragma unroll
-        for (int k = 0; k + 1 < kStages; ++k) idx[k] = idx[k + 1];
-        idx[kStages - 1] = point_of(j + 2 * kStages);
+        for (int st = 0; st + 1 < kStages; ++st)
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) idx[st][k] = idx[st + 1][k];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) idx[kStages - 1][k] = point_of(j + 2 * kStages, k);
     }
     cp_async_wait<0>();  // no copy may land after the CTA has exited
 
@@ -374,21 +398,21 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
         atomicAdd(&hdr->needed, (unsigned long long)(open ? (rg.y - rg.x) : s_maxstop));
 }
 
-template <int TS, int C, bool BF16>
+template <int TS, int RPT, int C, bool BF16>
 cudaError_t launch_fwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     const unsigned grid = (unsigned)vt.tiles_total;
     if (vt.mode == 0) {
-        constexpr size_t smem = bilinear_fwd_smem<TS, C, BF16>();
+        constexpr size_t smem = bilinear_fwd_smem<TS, RPT, C, BF16>();
         static bool set = false;
         if (!set) {
-            cudaError_t e = cudaFuncSetAttribute(k_blend_fwd_bilinear<TS, C, BF16>,
+            cudaError_t e = cudaFuncSetAttribute(k_blend_fwd_bilinear<TS, RPT, C, BF16>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             set = true;
         }
         ProfScope ps("blend_fwd", s);
-        k_blend_fwd_bilinear<TS, C, BF16><<<grid, TS * TS, smem, s>>>(vt, b.ranges, b.order, pts, b.rec,
-                                                                  b.t_final, b.last, b.hdr, b.trace);
+        k_blend_fwd_bilinear<TS, RPT, C, BF16><<<grid, TS * TS, smem, s>>>(
+            vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.hdr, b.trace);
         return cudaGetLastError();
     }
     ProfScope ps("blend_fwd", s);
@@ -397,11 +421,21 @@ cudaError_t launch_fwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts
     return cudaGetLastError();
 }
 
+template <int TS, int C, bool BF16>
+cudaError_t launch_fwd_d(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    const int rpt = vt.mode == 0 ? vt.blend_depth / (TS * TS) : 1;
+    if constexpr (TS == 8) {
+        if (rpt == 4) return launch_fwd_t<TS, 4, C, BF16>(vt, b, pts, s);
+    }
+    if (rpt == 2) return launch_fwd_t<TS, 2, C, BF16>(vt, b, pts, s);
+    return launch_fwd_t<TS, 1, C, BF16>(vt, b, pts, s);
+}
+
 template <int C>
 cudaError_t launch_fwd_c(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     if (vt.tile == 8)
-        return vt.bf16 ? launch_fwd_t<8, C, true>(vt, b, pts, s) : launch_fwd_t<8, C, false>(vt, b, pts, s);
-    return vt.bf16 ? launch_fwd_t<16, C, true>(vt, b, pts, s) : launch_fwd_t<16, C, false>(vt, b, pts, s);
+        return vt.bf16 ? launch_fwd_d<8, C, true>(vt, b, pts, s) : launch_fwd_d<8, C, false>(vt, b, pts, s);
+    return vt.bf16 ? launch_fwd_d<16, C, true>(vt, b, pts, s) : launch_fwd_d<16, C, false>(vt, b, pts, s);
 }
 
 }  // namespace

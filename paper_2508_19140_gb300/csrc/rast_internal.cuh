@@ -54,6 +54,7 @@ struct ViewTable {
     int32_t mode;        // 0 bilinear, 1 Gaussian
     int32_t gauss_cov;   // 0 EWA, 1 isotropic screen
     int32_t tile;        // tile edge in pixels (8 or 16)
+    int32_t blend_depth; // records per blend batch: tile^2 x {1, 2} (x 4 for tile 8); Gaussian: tile^2
     int32_t rec_words;   // record stride in 32-bit words (multiple of 4)
     int32_t feat_word;   // first feature word in a record
     float t_min, alpha_max, dilation;

@@ -124,8 +124,9 @@ def test_argument_validation_is_synchronous(lib):
     assert B(arr, 17, 1, ct.byref(o), ws, big, None) == rast.RAST_ERR_ARG
     assert B(arr, 1, 0, ct.byref(o), ws, big, None) == rast.RAST_ERR_ARG
     assert B(arr, 1, 1, ct.byref(_opts(lib, tile=32)), ws, big, None) == rast.RAST_ERR_NOT_SUPPORTED
-    assert B(arr, 1, 1, ct.byref(_opts(lib, tile=8, blend_depth=256)), ws, big, None) == \
-        rast.RAST_ERR_NOT_SUPPORTED
+    for t, d, m in ((8, 512, 0), (16, 1024, 0), (16, 300, 0), (16, 512, 1), (8, 128, 1)):
+        assert B(arr, 1, 1, ct.byref(_opts(lib, tile=t, blend_depth=d, mode=m)), ws, big, None) == \
+            rast.RAST_ERR_NOT_SUPPORTED, (t, d, m)
     assert B(arr, 1, 1, ct.byref(_opts(lib, mode=7)), ws, big, None) == rast.RAST_ERR_ARG
     assert B(arr, 1, 1, ct.byref(_opts(lib, alpha_max=1.0)), ws, big, None) == rast.RAST_ERR_ARG
     assert B(arr, 1, 1, ct.byref(o), None, big, None) == rast.RAST_ERR_ARG
