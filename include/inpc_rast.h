@@ -212,6 +212,14 @@ int32_t rasterize_workspace_layout(const rast_view_t* views, int32_t n_views,
 void rasterize_profile_enable(int32_t on);
 int32_t rasterize_profile_read(rast_profile_entry_t* out, int32_t max);
 
+/* Compiled (tile edge, blend depth) pairs for splat mode `mode`, in the
+ * order an autotuner should try them (the default first). Writes up to `max`
+ * pairs to tiles[] / depths[] (either may be NULL to only count) and returns
+ * how many exist; -1 for an unknown mode. Host only, no device access. The
+ * paper fixes 16x16 tiles (Sec. 3.2); the other pairs change only the work
+ * split, never the images (gradients agree to FP32 rounding). */
+int32_t rasterize_tune_candidates(int32_t mode, int32_t* tiles, int32_t* depths, int32_t max);
+
 /* Library version string. */
 const char* rasterize_version(void);
 

@@ -555,6 +555,21 @@ int32_t rasterize_profile_read(rast_profile_entry_t* out, int32_t max) {
     return n;
 }
 
+int32_t rasterize_tune_candidates(int32_t mode, int32_t* tiles, int32_t* depths, int32_t max) {
+    if (mode != RAST_SPLAT_BILINEAR && mode != RAST_SPLAT_GAUSSIAN) return -1;
+    static const int32_t kPairs[][2] = {{16, 256}, {16, 512}, {8, 64}, {8, 128}, {8, 256}};
+    int32_t n = 0;
+    for (const auto& pr : kPairs) {
+        if (!blend_depth_supported(mode, pr[0], pr[1])) continue;
+        if (n < max) {
+            if (tiles) tiles[n] = pr[0];
+            if (depths) depths[n] = pr[1];
+        }
+        ++n;
+    }
+    return n;
+}
+
 const char* rasterize_version(void) { return "inpc-rast-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"

@@ -104,6 +104,8 @@ SIGNATURES = {
                                                 ct.POINTER(WsEntry), ct.c_int32]),
     "rasterize_profile_enable": (None, [ct.c_int32]),
     "rasterize_profile_read": (ct.c_int32, [ct.POINTER(ProfileEntry), ct.c_int32]),
+    "rasterize_tune_candidates": (ct.c_int32, [ct.c_int32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
+                                               ct.c_int32]),
     "rasterize_version": (ct.c_char_p, []),
 }
 
@@ -292,6 +294,18 @@ def rasterize_profile_read() -> dict:
     n = L.rasterize_profile_read(ents, 64)
     return {ents[k].name.decode(): (int(ents[k].launches), float(ents[k].total_ms))
             for k in range(min(n, 64))}
+
+
+def rasterize_tune_candidates(mode="bilinear"):
+    """Compiled (tile, blend_depth) pairs for a splat mode, default first."""
+    m = {"bilinear": BILINEAR, "gaussian": GAUSSIAN}.get(mode, mode)
+    L = load_library()
+    n = L.rasterize_tune_candidates(int(m), None, None, 0)
+    if n < 0:
+        raise RastError(RAST_ERR_ARG, "rasterize_tune_candidates")
+    tiles, depths = (ct.c_int32 * max(n, 1))(), (ct.c_int32 * max(n, 1))()
+    L.rasterize_tune_candidates(int(m), tiles, depths, n)
+    return [(int(tiles[k]), int(depths[k])) for k in range(n)]
 
 
 def rasterize_version() -> str:
