@@ -352,13 +352,15 @@ cudaError_t run_fwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
                                       vt.pix_total);
         RAST_TRY(cudaGetLastError());
     }
-    RAST_TRY(launch_project(vt, b, s));
+    // The depth sort's first pass generates the point indices itself.
+    RAST_TRY(launch_project(vt, b, pl.planA.passes == 0, s));
     int ra = 0, rc = 0;
     {
         uint32_t* k[2] = {b.keyA[0], b.keyA[1]};
         uint32_t* v[2] = {b.valA[0], b.valA[1]};
         const SortScratch sc{b.sort_ghist, b.sort_counters, b.sort_status, &b.hdr->error};
-        RAST_TRY(radix_sort(k, v, vt.n_total, nullptr, vt.n_total, pl.planA, sc, s, &ra, kDepthSortNames));
+        RAST_TRY(radix_sort(k, v, vt.n_total, nullptr, vt.n_total, pl.planA, sc, s, &ra, kDepthSortNames,
+                            true));
     }
     const uint32_t* depth_sorted = b.valA[ra];
     RAST_TRY(launch_duplicate(vt, b, depth_sorted, s));

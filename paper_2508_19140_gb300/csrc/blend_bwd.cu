@@ -552,13 +552,15 @@ __global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const 
     float acc[P];
 #pragma unroll
     for (int k = 0; k < P; ++k) acc[k] = 0.f;
+    // Independent loads first: one memory round trip for all three.
     const uint2 rc = rect[gi];
+    const uint32_t zb = zbits[gi];
+    const uint32_t pbase = base[gi];
     const uint32_t cnt = rect_count(rc);
     bool written = false;  // bilinear: the blend wrote the sole copy's gradients itself
     if (cnt) {
-        const uint32_t zb = zbits[gi];
         const int tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff, ty1 = rc.y >> 16;
-        const float* pp = partial + (size_t)base[gi] * PS;
+        const float* pp = partial + (size_t)pbase * PS;
         int k = 0;
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx, ++k) {

@@ -44,31 +44,44 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp
 }
 
 constexpr int kT = 256;
-constexpr int kPer = kScanItems / kT;  // 4 items per thread, striped
+constexpr int kPer = kScanItems / kT;  // 4 consecutive items per thread
 
-// rectS[s] = rect[sorted_pts[s]]; block sums of the tile counts.
+// Sorted-order rects of a block of kScanItems points (gathered once, kept for
+// k_dup_write) and the block's copy count.
 __global__ void __launch_bounds__(kT) k_dup_count(const uint32_t* __restrict__ sorted_pts,
                                                   const uint2* __restrict__ rect,
                                                   uint2* __restrict__ rectS, int64_t n,
                                                   uint32_t* __restrict__ blk) {
     __shared__ uint32_t s_warp[33];
-    const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
+    const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
+    uint32_t gi[kPer];
+    if (s0 + kPer <= n) {
+        const uint4 q = *reinterpret_cast<const uint4*>(sorted_pts + s0);
+        gi[0] = q.x; gi[1] = q.y; gi[2] = q.z; gi[3] = q.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) gi[j] = s0 + j < n ? sorted_pts[s0 + j] : 0xffffffffu;
+    }
+    uint2 r[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) r[j] = gi[j] != 0xffffffffu ? rect[gi[j]] : make_uint2(1u, 0u);
     uint32_t c = 0;
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        const int64_t s = b0 + j * kT + threadIdx.x;
-        if (s < n) {
-            const uint2 r = rect[sorted_pts[s]];
-            rectS[s] = r;
-            c += rect_count(r);
-        }
+    for (int j = 0; j < kPer; ++j) c += rect_count(r[j]);
+    if (s0 + kPer <= n) {
+        uint4* d = reinterpret_cast<uint4*>(rectS + s0);
+        d[0] = make_uint4(r[0].x, r[0].y, r[1].x, r[1].y);
+        d[1] = make_uint4(r[2].x, r[2].y, r[3].x, r[3].y);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j)
+            if (s0 + j < n) rectS[s0 + j] = r[j];
     }
     uint32_t tot;
     block_excl_scan<kT>(c, s_warp, tot);
     if (threadIdx.x == 0) blk[blockIdx.x] = tot;
 }
 
-// Block sums of a per-point count array (point order).
 __global__ void __launch_bounds__(kT) k_count_blocks(const uint32_t* __restrict__ cnt, int64_t n,
                                                      uint32_t* __restrict__ blk) {
     __shared__ uint32_t s_warp[33];
@@ -126,34 +139,50 @@ __global__ void __launch_bounds__(kT) k_dup_write(const ViewTable vt, const uint
                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                   int64_t cap) {
     __shared__ uint32_t s_warp[33];
-    const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
-    uint32_t off = blk[blockIdx.x];
-#pragma unroll 1
+    const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
+    uint2 r[kPer];
+    uint32_t gi[kPer];
+    if (s0 + kPer <= n) {
+        const uint4* q = reinterpret_cast<const uint4*>(rectS + s0);
+        const uint4 a = q[0], b = q[1];
+        r[0] = make_uint2(a.x, a.y); r[1] = make_uint2(a.z, a.w);
+        r[2] = make_uint2(b.x, b.y); r[3] = make_uint2(b.z, b.w);
+        const uint4 g = *reinterpret_cast<const uint4*>(sorted_pts + s0);
+        gi[0] = g.x; gi[1] = g.y; gi[2] = g.z; gi[3] = g.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const bool ok = s0 + j < n;
+            r[j] = ok ? rectS[s0 + j] : make_uint2(1u, 0u);
+            gi[j] = ok ? sorted_pts[s0 + j] : 0u;
+        }
+    }
+    uint32_t c[kPer], sum = 0;
+#pragma unroll
     for (int j = 0; j < kPer; ++j) {
-        const int64_t s = b0 + j * kT + threadIdx.x;
-        uint2 r = make_uint2(1u, 0u);
-        if (s < n) r = rectS[s];
-        const uint32_t c = rect_count(r);
-        uint32_t tot;
-        uint32_t o = off + block_excl_scan<kT>(c, s_warp, tot);
-        off += tot;
-        if (c) {
-            const uint32_t gi = sorted_pts[s];
-            const ViewDev& V = vt.v[view_of_point(vt, gi)];
-            const int tx0 = r.x & 0xffff, ty0 = r.x >> 16, tx1 = r.y & 0xffff, ty1 = r.y >> 16;
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) {
-                    if ((int64_t)o < cap) {
-                        keys[o] = (uint32_t)(V.tile_off + (int64_t)ty * V.tiles_x + tx);
-                        vals[o] = gi;
-                    }
-                    ++o;
+        c[j] = rect_count(r[j]);
+        sum += c[j];
+    }
+    uint32_t tot;
+    uint32_t o = blk[blockIdx.x] + block_excl_scan<kT>(sum, s_warp, tot);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        if (c[j] == 0) continue;
+        const ViewDev& V = vt.v[view_of_point(vt, gi[j])];
+        const int tx0 = r[j].x & 0xffff, ty0 = r[j].x >> 16, tx1 = r[j].y & 0xffff, ty1 = r[j].y >> 16;
+        for (int ty = ty0; ty <= ty1; ++ty) {
+            const uint32_t row = (uint32_t)(V.tile_off + (int64_t)ty * V.tiles_x);
+            for (int tx = tx0; tx <= tx1; ++tx) {
+                if ((int64_t)o < cap) {
+                    keys[o] = row + (uint32_t)tx;
+                    vals[o] = gi[j];
                 }
+                ++o;
+            }
         }
     }
 }
 
-// base[i] = exclusive prefix of cnt in point order.
 __global__ void __launch_bounds__(kT) k_scan_apply(const uint32_t* __restrict__ cnt, int64_t n,
                                                    const uint32_t* __restrict__ blk,
                                                    uint32_t* __restrict__ base) {

@@ -20,7 +20,7 @@ namespace rast {
 namespace {
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs b) {
+__global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs b, bool write_vals) {
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= vt.n_total) return;
     const int vi = view_of_point(vt, gi);
@@ -132,15 +132,24 @@ __global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs 
             }
         } else {
             const unsigned short* f = static_cast<const unsigned short*>(V.feat) + i * C;
-            for (int c = 0; c < C; c += 2) {
-                const uint32_t lo = f[c];
-                const uint32_t hi = (c + 1 < C) ? f[c + 1] : 0u;
-                fw[c >> 1] = lo | (hi << 16);
+            const uintptr_t fa = reinterpret_cast<uintptr_t>(f);
+            if ((C & 7) == 0 && (fa & 15) == 0) {
+                for (int c = 0; c < C; c += 8)
+                    *reinterpret_cast<uint4*>(fw + (c >> 1)) = *reinterpret_cast<const uint4*>(f + c);
+            } else if ((C & 3) == 0 && (fa & 7) == 0) {
+                for (int c = 0; c < C; c += 4)
+                    *reinterpret_cast<uint2*>(fw + (c >> 1)) = *reinterpret_cast<const uint2*>(f + c);
+            } else {
+                for (int c = 0; c < C; c += 2) {
+                    const uint32_t lo = f[c];
+                    const uint32_t hi = (c + 1 < C) ? f[c + 1] : 0u;
+                    fw[c >> 1] = lo | (hi << 16);
+                }
             }
         }
     }
     b.keyA[0][gi] = key;
-    b.valA[0][gi] = (uint32_t)gi;
+    if (write_vals) b.valA[0][gi] = (uint32_t)gi;
     b.rect[gi] = rect;
     b.cnt[gi] = count;
     b.zbits[gi] = __float_as_uint(zc);
@@ -148,12 +157,12 @@ __global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs 
 
 }  // namespace
 
-cudaError_t launch_project(const ViewTable& vt, const Bufs& b, cudaStream_t s) {
+cudaError_t launch_project(const ViewTable& vt, const Bufs& b, bool write_vals, cudaStream_t s) {
     if (vt.n_total == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((vt.n_total + 255) / 256);
     ProfScope ps("project", s);
-    if (vt.mode == 0) k_project<0><<<grid, 256, 0, s>>>(vt, b);
-    else k_project<1><<<grid, 256, 0, s>>>(vt, b);
+    if (vt.mode == 0) k_project<0><<<grid, 256, 0, s>>>(vt, b, write_vals);
+    else k_project<1><<<grid, 256, 0, s>>>(vt, b, write_vals);
     return cudaGetLastError();
 }
 

@@ -78,9 +78,9 @@ struct WsHeader {
 
 __device__ __forceinline__ int view_of_point(const ViewTable& vt, int64_t gi) {
     int v = 0;
-#pragma unroll 1
-    for (int k = 1; k < vt.n_views; ++k)
-        if (gi >= vt.v[k].pt_off) v = k;
+#pragma unroll
+    for (int k = 1; k < kMaxViews; ++k)
+        if (k < vt.n_views && gi >= vt.v[k].pt_off) v = k;
     return v;
 }
 
@@ -197,14 +197,18 @@ struct SortScratch {
     uint32_t* err;       // workspace error word
 };
 
-cudaError_t launch_project(const ViewTable& vt, const Bufs& b, cudaStream_t s);
+// write_vals: also write the identity point values into valA[0] (needed only
+// when the depth sort makes no pass).
+cudaError_t launch_project(const ViewTable& vt, const Bufs& b, bool write_vals, cudaStream_t s);
 // Stable LSD radix sort of (key, val) pairs in keys[0]/vals[0] using keys[1]/vals[1]
 // as scratch; count from d_n (device) if non-null else n (at most cap). Sets
 // *result_buf to the index (0/1) of the buffer that holds the result.
 // names: profiling names of the digit-count kernel and of the sweep passes.
+// identity_vals: the input values are their own positions (0, 1, 2, ...);
+// vals[0] is then not read.
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n, int64_t cap,
                        const SortPlan& plan, const SortScratch& sc, cudaStream_t s, int* result_buf,
-                       const char* const names[2]);
+                       const char* const names[2], bool identity_vals = false);
 cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
                              cudaStream_t s);
 cudaError_t launch_ranges(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_tiles,

@@ -38,7 +38,7 @@ constexpr int kWarpItems = 32 * kIPT;       // 512 keys per warp
 constexpr uint32_t kFlagAgg = 1u << 30;     // tile count published
 constexpr uint32_t kFlagPrefix = 2u << 30;  // inclusive prefix over tiles 0..t published
 constexpr uint32_t kValueMask = (1u << 30) - 1;
-constexpr int kLookback = 8;                // predecessor tiles read per look-back step
+constexpr int kLookback = 8;               // predecessor tiles read per look-back step
 
 int num_sms() {
     static int n = 0;
@@ -110,17 +110,32 @@ __global__ void __launch_bounds__(kThreads) k_digit_hist(const uint32_t* __restr
             st[i] = 0;
     }
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-        const uint32_t k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * BINS + ((k >> (p * BITS)) & (BINS - 1))], 1u);
+    // Eight independent loads in flight per thread before the shared-memory
+    // counting (one load at a time leaves the kernel waiting on latency).
+    constexpr int U = 8;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t i0 = (int64_t)blockIdx.x * kThreads + threadIdx.x; i0 < n; i0 += U * stride) {
+        uint32_t k[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            k[u] = i < n ? keys[i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i0 + u * stride >= n) break;
+            for (int p = 0; p < passes; ++p)
+                atomicAdd(&s_h[p * BINS + ((k[u] >> (p * BITS)) & (BINS - 1))], 1u);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * BINS; i += kThreads)
         if (s_h[i]) atomicAdd(&ghist[i], s_h[i]);
 }
 
-template <int BITS>
-__global__ void __launch_bounds__(kThreads) k_sweep(
+// IDV: the input values are their positions (not read from memory).
+template <int BITS, bool IDV>
+__global__ void __launch_bounds__(kThreads, 3) k_sweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n_host, const uint32_t* d_n, int shift,
     const uint32_t* __restrict__ ghist_pass, uint32_t* __restrict__ counter, uint32_t* __restrict__ status,
@@ -128,9 +143,10 @@ __global__ void __launch_bounds__(kThreads) k_sweep(
     constexpr int BINS = 1 << BITS;
     constexpr int VPT = BINS > kThreads ? BINS / kThreads : 1;
     extern __shared__ uint32_t smem[];
-    uint32_t* s_keys = smem;                       // kSortTile
-    uint32_t* s_vals = s_keys + kSortTile;         // kSortTile
-    uint32_t* s_whist = s_vals + kSortTile;        // 8 * BINS: per-warp counts, then prefixes
+    uint32_t* s_keys = smem;                       // kSortTile: keys in digit order
+    uint32_t* s_vals = s_keys + kSortTile;         // kSortTile: values in digit order
+    uint32_t* s_vin = s_vals + kSortTile;          // kSortTile: values in input order
+    uint32_t* s_whist = s_vin + kSortTile;         // 8 * BINS: per-warp counts, then prefixes
     uint32_t* s_excl = s_whist + 8 * BINS;         // BINS: tile-local digit starts
     uint32_t* s_gbase = s_excl + BINS;             // BINS: global digit starts of this tile
     uint32_t* s_goff = s_gbase + BINS;             // BINS: global digit starts of the pass
@@ -168,20 +184,24 @@ __global__ void __launch_bounds__(kThreads) k_sweep(
         if (tile >= ntiles) break;
         const int64_t base = tile * kSortTile;
         const int64_t wbase = base + warp * kWarpItems;
-        uint32_t k[kIPT], v[kIPT];
+        // Keys to registers; values straight to shared memory in input order
+        // (they are only moved, never inspected).
+        uint32_t k[kIPT];
 #pragma unroll
         for (int r = 0; r < kIPT; ++r) {
             const int64_t idx = wbase + r * 32 + lane;
             const bool ok = idx < n;
             k[r] = ok ? kin[idx] : 0u;
-            v[r] = ok ? vin[idx] : 0u;
+            s_vin[warp * kWarpItems + r * 32 + lane] = ok ? (IDV ? (uint32_t)idx : vin[idx]) : 0u;
         }
         for (int i = threadIdx.x; i < 8 * BINS; i += kThreads) s_whist[i] = 0;
         __syncthreads();
 
         // Stable rank inside the warp's 512 keys: rounds in input order, lanes
-        // in order within a round.
-        uint32_t lp[kIPT];
+        // in order within a round. Ranks (< 512) are kept two to a register.
+        uint32_t lp[kIPT / 2];
+#pragma unroll
+        for (int r = 0; r < kIPT / 2; ++r) lp[r] = 0;
 #pragma unroll
         for (int r = 0; r < kIPT; ++r) {
             const int64_t idx = wbase + r * 32 + lane;
@@ -197,12 +217,14 @@ __global__ void __launch_bounds__(kThreads) k_sweep(
                 const uint32_t m = __ballot_sync(0xffffffffu, set);
                 peers &= set ? m : ~m;
             }
+            // The first lane of each digit group adds the group to the warp's
+            // counter (atomics of one warp to one address apply in program
+            // order, so rounds need no barrier) and hands the old value on.
+            const int leader = __ffs(peers) - 1;
             uint32_t pre = 0;
-            if (ok) pre = s_whist[warp * BINS + d];
-            __syncwarp();
-            if (ok && (peers & lt) == 0) s_whist[warp * BINS + d] = pre + __popc(peers);
-            __syncwarp();
-            lp[r] = pre + __popc(peers & lt);
+            if (ok && lane == leader) pre = atomicAdd(&s_whist[warp * BINS + d], (uint32_t)__popc(peers));
+            pre = __shfl_sync(0xffffffffu, pre, leader);
+            lp[r >> 1] |= (pre + __popc(peers & lt)) << ((r & 1) * 16);
         }
         __syncthreads();
 
@@ -299,9 +321,10 @@ __global__ void __launch_bounds__(kThreads) k_sweep(
             const int64_t idx = wbase + r * 32 + lane;
             if (idx < n) {
                 const uint32_t d = (k[r] >> shift) & (BINS - 1);
-                const uint32_t pos = s_excl[d] + s_whist[warp * BINS + d] + lp[r];
+                const uint32_t rank = (lp[r >> 1] >> ((r & 1) * 16)) & 0xffffu;
+                const uint32_t pos = s_excl[d] + s_whist[warp * BINS + d] + rank;
                 s_keys[pos] = k[r];
-                s_vals[pos] = v[r];
+                s_vals[pos] = s_vin[warp * kWarpItems + r * 32 + lane];
             }
         }
         __syncthreads();
@@ -321,19 +344,21 @@ __global__ void __launch_bounds__(kThreads) k_sweep(
 template <int BITS>
 size_t sweep_smem() {
     constexpr int BINS = 1 << BITS;
-    return sizeof(uint32_t) * (2 * kSortTile + 8 * BINS + 3 * BINS + 33 + 1);
+    return sizeof(uint32_t) * (3 * kSortTile + 8 * BINS + 3 * BINS + 33 + 1);
 }
 
 template <int BITS>
 cudaError_t sort_t(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n, int64_t cap,
                    const SortPlan& plan, const SortScratch& sc, cudaStream_t s, int* result_buf,
-                   const char* const names[2]) {
+                   const char* const names[2], bool identity_vals) {
     constexpr int BINS = 1 << BITS;
     static bool attr_set = false;
     const size_t smem = sweep_smem<BITS>();
     if (!attr_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_sweep<BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_sweep<BITS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sweep<BITS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -351,11 +376,22 @@ cudaError_t sort_t(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    const unsigned gs = (unsigned)(tiles_cap < (int64_t)sms * 2 ? tiles_cap : (int64_t)sms * 2);
+    // Persistent grid: as many CTAs as fit on the GPU at once (every CTA
+    // resident, so a look-back never waits on a tile no running CTA holds).
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<BITS, false>, kThreads, smem) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
+    const int64_t resident = (int64_t)sms * per_sm;
+    const unsigned gs = (unsigned)(tiles_cap < resident ? tiles_cap : resident);
     int cur = 0;
     for (int k = 0; k < plan.passes; ++k) {
         ProfScope ps(names[1], s);
-        k_sweep<BITS><<<gs, kThreads, smem, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, d_n,
+        auto kern = (k == 0 && identity_vals) ? k_sweep<BITS, true> : k_sweep<BITS, false>;
+        kern<<<gs, kThreads, smem, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, d_n,
                                                  plan.shift[k], sc.ghist + k * BINS, sc.counters + k,
                                                  sc.status + (int64_t)k * tiles_cap * BINS, sc.err);
         e = cudaGetLastError();
@@ -394,16 +430,16 @@ int64_t sort_status_words(const SortPlan& plan, int64_t cap) {
 
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n, int64_t cap,
                        const SortPlan& plan, const SortScratch& sc, cudaStream_t s, int* result_buf,
-                       const char* const names[2]) {
+                       const char* const names[2], bool identity_vals) {
     *result_buf = 0;
     if (plan.passes == 0 || cap == 0) return cudaSuccess;
     switch (plan.digit_bits[0]) {
-        case 4: return sort_t<4>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
-        case 5: return sort_t<5>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
-        case 6: return sort_t<6>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
-        case 7: return sort_t<7>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
-        case 8: return sort_t<8>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
-        case 9: return sort_t<9>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names);
+        case 4: return sort_t<4>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
+        case 5: return sort_t<5>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
+        case 6: return sort_t<6>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
+        case 7: return sort_t<7>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
+        case 8: return sort_t<8>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
+        case 9: return sort_t<9>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
         default: return cudaErrorInvalidValue;
     }
 }
