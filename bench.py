@@ -128,16 +128,28 @@ def measured_peak_hbm():
 
 # ----------------------------------------------------------------------------- algorithmic bytes
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one
+# ncu capture of the kernel as it is built now, keyed by (kernel, workload id,
+# tile edge, blend depth). Random 32-byte record gathers and gradient-row
+# scatters move 64-byte DRAM bursts, hence traffic above the algorithmic bytes.
+MEASURED_TRAFFIC = {
+    ("blend_bwd", 2, 8, 128): 917298176,
+    ("blend_fwd", 2, 8, 128): 326646784,
+}
+
 def kernel_bytes(name, w):
     """Algorithmic DRAM bytes of ONE launch of kernel `name` on workload counts w."""
     N, D, Dn, Db, HW, C, P = w["N"], w["D"], w["needed"], w["needed_bwd"], w["HW"], w["C"], w["P"]
     rec, fb, npart = w["rec_bytes"], w["feat_bytes"], w["partial_floats"]
-    if name == "project":
-        return N * (12 + 4 + C * fb) + N * (rec + 4 + 4 + 8 + 4)
+    if name == "project":   # read xyz, opacity, features; write record, key, rect, count, depth bits
+        return N * (12 + 4 + C * fb) + N * (rec + 4 + 8 + 4 + 4)
     if name.endswith(".hist"):      # one read of the keys counts every pass's digits
         return 4 * (N if name.startswith("depth") else D)
     if name.endswith(".sweep"):     # per pass: read key+value, write key+value
-        return 16 * (N if name.startswith("depth") else D)
+        if name.startswith("depth"):  # the first pass makes the point indices itself
+            passes = max(w.get("depth_passes", 1), 1)
+            return (16 * passes - 4) * N / passes
+        return 16 * D
     if name == "dup.count":
         return N * (4 + 8 + 8)
     if name == "dup.write":
@@ -150,8 +162,8 @@ def kernel_bytes(name, w):
         return N * 4
     if name == "point_scan.apply":
         return N * 8
-    if name == "blend_bwd":
-        return Db * (rec + 4 + 12 + 4 * npart) + P * 16 + HW * (4 * C + 16)
+    if name == "blend_bwd":   # replayed records + indices, one gradient row per copy, pixel state
+        return Db * (rec + 4 + 4 * npart) + P * 16 + HW * (4 * C + 16)
     if name == "reduce_grads":
         return N * (8 + 4 + 4) + Db * 4 * npart + N * (4 * C + 4)
     return 0
@@ -374,7 +386,8 @@ def run_ours(args, ws_, rank, local):
              needed_bwd=int(stats["needed_records_bwd"]),
              HW=sum(v.camera.width * v.camera.height for v in scene.views), C=C,
              P=int(stats["n_tiles"]), rec_bytes=rec_bytes, feat_bytes=2 if bf16 else 4,
-             partial_floats=C + (7 if gauss else 1))
+             partial_floats=C + (7 if gauss else 1),
+             depth_passes=int(round(prof.get("depth_sort.sweep", (0, 0))[0] / max(prof.get("init_header", (1, 0))[0], 1))))
     peak, peak_src = measured_peak_hbm()
     kernels = {}
     for name, (launches, tot) in prof.items():
@@ -388,9 +401,12 @@ def run_ours(args, ws_, rank, local):
     if dom:
         k = kernels[dom]
         ach = k["gbs"] or 0.0
+        tkey = (dom, scene.config_id, int(opts.tile), int(opts.blend_depth) or int(opts.tile) ** 2)
+        traffic = MEASURED_TRAFFIC.get(tkey) if args.scale_points == 1.0 else None
         roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": round(ach / peak, 4), "traffic": None,
-                    "peak_source": f"{peak_src} (hbm_gbs)"}
+                    "frac": round(ach / peak, 4), "traffic": traffic,
+                    "algorithmic_bytes": k["bytes"],
+                    "peak_source": f"{peak_src} (hbm_gbs, copy burst)"}
     blend = kernels.get("blend_fwd")
     prof_steps = args.steps if graph is None else max(3, args.steps // 2)
     gpu_launches = int(round(sum(x[0] for x in prof.values()) / max(prof_steps, 1) * args.steps))
