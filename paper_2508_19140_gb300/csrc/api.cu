@@ -37,13 +37,13 @@ int bit_length(uint64_t x) {
 
 enum Slot {
     S_HDR, S_REC, S_RECT, S_CNT, S_ZBITS, S_KEYA0, S_KEYA1, S_VALA0, S_VALA1, S_RECTS, S_BASE, S_BLK,
-    S_KEYC0, S_KEYC1, S_VALC0, S_VALC1, S_PARTIAL, S_SGHIST, S_SCOUNT, S_SSTATUS, S_RANGES, S_ORDER, S_CUTOFF, S_TRACE,
+    S_KEYC0, S_KEYC1, S_VALC0, S_VALC1, S_PARTIAL, S_GROW, S_SGHIST, S_SCOUNT, S_SSTATUS, S_RANGES, S_ORDER, S_CUTOFF, S_TRACE,
     S_TFINAL, S_LAST, S_COUNT
 };
 const char* kSlotNames[S_COUNT] = {
     "header", "records", "rect", "count", "zbits", "keys_a0", "keys_a1", "vals_a0", "vals_a1",
     "rect_sorted", "base", "block_sums", "keys_c0", "keys_c1", "vals_c0", "vals_c1",
-    "partial", "sort_hist", "sort_counters", "sort_status", "ranges", "tile_order", "cutoff", "tile_trace", "t_final", "last"};
+    "partial", "grad_rows", "sort_hist", "sort_counters", "sort_status", "ranges", "tile_order", "cutoff", "tile_trace", "t_final", "last"};
 
 struct Plan {
     ViewTable vt;
@@ -183,6 +183,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     pl.bytes[S_BLK] = (size_t)pl.blk_cap * 4;
     pl.bytes[S_KEYC0] = pl.bytes[S_KEYC1] = pl.bytes[S_VALC0] = pl.bytes[S_VALC1] = (size_t)D * 4;
     pl.bytes[S_PARTIAL] = (size_t)D * pl.partial_floats * 4;
+    pl.bytes[S_GROW] = o->mode == RAST_SPLAT_BILINEAR ? (size_t)N * grow_stride(C + 1) * 4 : 0;
     pl.bytes[S_SGHIST] = (size_t)4 * 512 * 4;
     pl.bytes[S_SCOUNT] = (size_t)4 * 4;
     {
@@ -262,6 +263,7 @@ Bufs make_bufs(const Plan& pl, void* ws) {
     b.valC[0] = (uint32_t*)at(S_VALC0);
     b.valC[1] = (uint32_t*)at(S_VALC1);
     b.partial = (float*)at(S_PARTIAL);
+    b.grow = (float*)at(S_GROW);
     b.sort_ghist = (uint32_t*)at(S_SGHIST);
     b.sort_counters = (uint32_t*)at(S_SCOUNT);
     b.sort_status = (uint32_t*)at(S_SSTATUS);

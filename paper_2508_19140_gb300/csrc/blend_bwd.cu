@@ -17,9 +17,12 @@
 // to one copy are combined in a fixed order inside the CTA (bilinear: the copy
 // owns four slots, one per pixel of its 2x2 box; Gaussian: one slot per warp,
 // filled by a fixed-order shuffle reduction), and written to the copy's own
-// slot base[i] + (rank of the tile in the point's tile rect). K8 then sums a
-// point's slots in rect order. A per-tile cutoff (depth bits and point index of
-// the last record the replay touched) tells K8 which slots were written.
+// slot base[i] + (rank of the tile in the point's tile rect); a bilinear point
+// with a single copy writes its row to a per-point array instead (whole
+// sectors, no slot base needed). K8 then sums a point's slots in rect order and
+// writes the outputs with coalesced stores. A per-tile cutoff (depth bits and
+// point index of the last record the replay touched) tells K8 which slots were
+// written.
 #include "blend_common.cuh"
 
 namespace rast {
@@ -57,8 +60,8 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec,
     const float* __restrict__ t_final, const uint32_t* __restrict__ last_in,
-    const uint32_t* __restrict__ base, float* __restrict__ partial, uint2* __restrict__ cutoff,
-    WsHeader* __restrict__ hdr, unsigned long long* __restrict__ trace) {
+    const uint32_t* __restrict__ base, float* __restrict__ partial, float* __restrict__ grow,
+    uint2* __restrict__ cutoff, WsHeader* __restrict__ hdr, unsigned long long* __restrict__ trace) {
     constexpr int NT = TS * TS;  // threads = pixels
     constexpr int D = NT * RPT;  // records per batch
     constexpr int MW = D / 32;   // mask words per pixel
@@ -67,6 +70,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
     const long long c_start = clock64();
     constexpr int P = C + 1;  // dfeat[C], dopacity
     constexpr int PS = partial_stride(P);
+    constexpr int GS = grow_stride(P);
     constexpr int RW = RecLayout<0, C, BF16>::words;
     constexpr int FW = RecLayout<0, C, BF16>::feat_word;
     extern __shared__ __align__(128) uint32_t s_dyn[];
@@ -305,10 +309,12 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
                 acc[C] += s_da[sl * D + r];
             }
             if (single[k]) {
-                // Sole copy: write the point's gradients (K8 leaves them alone).
-                const int64_t i = (int64_t)gi_rec[k] - V.pt_off;
-                if (V.d_feat) store_row<C>(V.d_feat + i * C, acc);
-                if (V.d_opacity) V.d_opacity[i] = acc[C];
+                // Sole copy: the point's gradient, in a whole-sector row of its own
+                // (K8 copies it to the outputs with coalesced writes).
+                float row[GS];
+#pragma unroll
+                for (int q = 0; q < GS; ++q) row[q] = q < P ? acc[q] : 0.f;
+                store_row<GS>(grow + (size_t)gi_rec[k] * GS, row);
             } else {
                 float row[PS];
 #pragma unroll
@@ -542,9 +548,11 @@ __global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const 
                                                       const uint2* __restrict__ rect,
                                                       const uint32_t* __restrict__ base,
                                                       const uint2* __restrict__ cutoff,
-                                                      const float* __restrict__ partial) {
+                                                      const float* __restrict__ partial,
+                                                      const float* __restrict__ grow) {
     constexpr int P = MODE == 0 ? C + 1 : C + 7;
     constexpr int PS = partial_stride(P);
+    constexpr int GS = grow_stride(P);
     const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= vt.n_total) return;
     const ViewDev& V = vt.v[view_of_point(vt, gi)];
@@ -557,7 +565,6 @@ __global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const 
     const uint32_t zb = zbits[gi];
     const uint32_t pbase = base[gi];
     const uint32_t cnt = rect_count(rc);
-    bool written = false;  // bilinear: the blend wrote the sole copy's gradients itself
     if (cnt) {
         const int tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff, ty1 = rc.y >> 16;
         const float* pp = partial + (size_t)pbase * PS;
@@ -567,11 +574,9 @@ __global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const 
                 const uint2 co = cutoff[V.tile_off + (int64_t)ty * V.tiles_x + tx];
                 const bool done = zb < co.x || (zb == co.x && (uint32_t)gi <= co.y);
                 if (!done) continue;
-                if (MODE == 0 && cnt == 1) {
-                    written = true;
-                    continue;
-                }
-                const float4* row = reinterpret_cast<const float4*>(pp + (size_t)k * PS);
+                // Bilinear points with one copy have their row indexed by point.
+                const bool own = MODE == 0 && cnt == 1;
+                const float4* row = reinterpret_cast<const float4*>(own ? grow + (size_t)gi * GS : pp + (size_t)k * PS);
 #pragma unroll
                 for (int j = 0; j < PS / 4; ++j) {
                     const float4 x = row[j];
@@ -582,10 +587,8 @@ __global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const 
                 }
             }
     }
-    if (!written) {
-        if (V.d_feat) store_row<C>(V.d_feat + i * C, acc);
-        if (V.d_opacity) V.d_opacity[i] = acc[C];
-    }
+    if (V.d_feat) store_row<C>(V.d_feat + i * C, acc);
+    if (V.d_opacity) V.d_opacity[i] = acc[C];
     if (MODE == 0) {
         if (V.d_xyz) {
             V.d_xyz[3 * i] = 0.f;
@@ -677,7 +680,7 @@ cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts
         }
         ProfScope ps("blend_bwd", s);
         k_blend_bwd_bilinear<TS, RPT, C, BF16><<<grid, TS * TS, smem, s>>>(
-            vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.cutoff, b.hdr,
+            vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.grow, b.cutoff, b.hdr,
             b.trace);
     } else {
         constexpr int NT = TS * TS;
@@ -719,9 +722,9 @@ cudaError_t launch_reduce_c(const ViewTable& vt, const Bufs& b, cudaStream_t s) 
     const unsigned grid = (unsigned)((vt.n_total + 255) / 256);
     ProfScope ps("reduce_grads", s);
     if (vt.mode == 0)
-        k_reduce_grads<C, 0><<<grid, 256, 0, s>>>(vt, b.zbits, b.rect, b.base, b.cutoff, b.partial);
+        k_reduce_grads<C, 0><<<grid, 256, 0, s>>>(vt, b.zbits, b.rect, b.base, b.cutoff, b.partial, b.grow);
     else
-        k_reduce_grads<C, 1><<<grid, 256, 0, s>>>(vt, b.zbits, b.rect, b.base, b.cutoff, b.partial);
+        k_reduce_grads<C, 1><<<grid, 256, 0, s>>>(vt, b.zbits, b.rect, b.base, b.cutoff, b.partial, b.grow);
     return cudaGetLastError();
 }
 

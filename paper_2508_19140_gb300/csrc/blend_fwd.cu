@@ -121,6 +121,9 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
 #pragma unroll
     for (int w = 0; w < MW; ++w) s_mask[tid][w] = 0;
     if (tid == 0) s_maxstop = 0;
+    // Every row must be clear before any record thread sets bits in another
+    // pixel's row (the first batch's atomicOr).
+    __syncthreads();
 
     // Thread t copies records t, t + NT, ... of every batch. idx[s] = point
     // indices of batch j + kStages + s while batch j is processed (the copies

@@ -129,6 +129,12 @@ __device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w &
 // multiple of 4 so every row is written and read as 16-byte vectors.
 __host__ __device__ constexpr int partial_stride(int P) { return (P + 3) & ~3; }
 
+// Row stride (floats) of the per-point gradient rows of single-copy points:
+// a power of two >= P, so each row is whole 32-byte sectors (C <= 7) or whole
+// 64-byte bursts (8 <= C <= 15) and a scattered row write never merges with a
+// neighbour's bytes.
+__host__ __device__ constexpr int grow_stride(int P) { return P <= 4 ? 4 : (P <= 8 ? 8 : (P <= 16 ? 16 : 32)); }
+
 __device__ __forceinline__ uint32_t rect_count(uint2 r) {
     const int tx0 = r.x & 0xffff, ty0 = r.x >> 16, tx1 = r.y & 0xffff, ty1 = r.y >> 16;
     if (tx1 < tx0 || ty1 < ty0) return 0;
@@ -162,7 +168,8 @@ struct Bufs {
     // per copy
     uint32_t* keyC[2];
     uint32_t* valC[2];
-    float* partial;       // backward per-copy partial gradients
+    float* partial;       // backward per-copy partial gradients (points with several copies)
+    float* grow;          // backward gradient rows of single-copy points, indexed by point
     // radix sort scratch
     uint32_t* sort_ghist;     // [passes][bins] digit counts
     uint32_t* sort_counters;  // [4] tile counters of the passes
