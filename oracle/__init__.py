@@ -16,6 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
+_SRCS = [_SRC, os.path.join(_HERE, "envmap.cpp")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -41,11 +42,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle (g++, -ffp-contract=off so FP32 decisions round op by op)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", _SRC, "-o", tmp]
+           "-fno-fast-math", *_SRCS, "-o", tmp]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -69,6 +70,12 @@ def lib():
             L.orc_backward.argtypes = [ct.c_int64, P, P, P, P, ct.c_int32, P, P, P, P, P, P,
                                        P, P, P, P]
             L.orc_backward.restype = None
+            L.orc_env_dirs.argtypes = [P, P]
+            L.orc_env_dirs.restype = None
+            L.orc_env_composite.argtypes = [P, P, ct.c_int32, ct.c_int32, ct.c_int32, P, P, P, P, P]
+            L.orc_env_composite.restype = None
+            L.orc_env_backward.argtypes = [P, P, ct.c_int32, ct.c_int32, ct.c_int32, P, P, P, P, P]
+            L.orc_env_backward.restype = None
             _lib = L
     return _lib
 
@@ -188,3 +195,42 @@ def backward(xyz, opacity, feat, camera, g_feat, g_alpha=None, g_depth=None, sca
                        _ptr(out["d_feat"]), _ptr(out["d_opacity"]), _ptr(out["d_xyz"]),
                        _ptr(out["d_scale"]))
     return out
+
+
+# ----------------------------------------------------------------------------- background model
+
+def env_dirs(camera):
+    """Camera-space unit viewing direction of every pixel (H x W x 3), FP64."""
+    cam = make_camera(camera)
+    out = np.zeros((camera.height, camera.width, 3))
+    lib().orc_env_dirs(ct.byref(cam), _ptr(out))
+    return out
+
+
+def env_composite(env, camera, F, alpha, dirs=None):
+    """Sec. 3.2 "Faster Background Model Evaluation": out = F + (1 - alpha) f_bg,
+    f_bg the bilinear lookup of the spherical map `env` (H_b x W_b x C) along each
+    pixel's viewing direction. Returns (out, f_bg)."""
+    env = _f64(env)
+    Hb, Wb, C = env.shape
+    cam = make_camera(camera)
+    F, alpha, dirs = _f64(F), _f64(alpha), _f64(dirs)
+    out = np.zeros(F.shape)
+    bg = np.zeros(F.shape)
+    lib().orc_env_composite(ct.byref(cam), _ptr(env), Hb, Wb, C, _ptr(dirs), _ptr(F), _ptr(alpha),
+                            _ptr(out), _ptr(bg))
+    return out, bg
+
+
+def env_backward(env, camera, alpha, g, dirs=None):
+    """Adjoint of env_composite for upstream gradient g (H x W x C): returns
+    (dL/dalpha [H x W], dL/dmap [H_b x W_b x C]); dL/dF is g itself."""
+    env = _f64(env)
+    Hb, Wb, C = env.shape
+    cam = make_camera(camera)
+    alpha, g, dirs = _f64(alpha), _f64(g), _f64(dirs)
+    d_alpha = np.zeros(alpha.shape)
+    d_map = np.zeros(env.shape)
+    lib().orc_env_backward(ct.byref(cam), _ptr(env), Hb, Wb, C, _ptr(dirs), _ptr(alpha), _ptr(g),
+                           _ptr(d_alpha), _ptr(d_map))
+    return d_alpha, d_map

@@ -234,3 +234,28 @@ def random_small_view(seed, n, width, height, c=4, gaussian=False, f=None,
     gf, ga, gd = _grads(rng, cam, c)
     return View(xyz=xyz, opacity=o, feat=feat, camera=cam, scale=scale,
                 g_feat=gf, g_alpha=ga, g_depth=gd)
+
+
+def env_map(seed=2001, height=1024, width=2048, c=4, kind="smooth"):
+    """Synthetic stand-in for the distilled spherical background map
+    (H_b x W_b x C FP32; the paper's map is 1024 x 2048 x 4).
+
+    kind="smooth": a low-frequency field (sky-like: a vertical gradient plus a
+    few long-wavelength waves in longitude and polar angle), values in
+    (0.05, 0.95); kind="noise": i.i.d. U(0, 1) texels (worst case for
+    interpolation error)."""
+    rng = np.random.default_rng(seed)
+    if kind == "noise":
+        return rng.uniform(0.0, 1.0, (height, width, c)).astype(np.float32)
+    lam = (np.arange(width) + 0.5) / width * 2.0 * np.pi - np.pi
+    th = (np.arange(height) + 0.5) / height * np.pi
+    L, TH = np.meshgrid(lam, th)
+    out = np.empty((height, width, c), np.float64)
+    for ch in range(c):
+        k = rng.integers(1, 4, 3)
+        ph = rng.uniform(0, 2 * np.pi, 3)
+        v = 0.5 + 0.25 * np.cos(TH + ph[0])
+        v += 0.1 * np.cos(k[0] * L + ph[1]) * np.sin(TH)
+        v += 0.05 * np.cos(k[1] * L + k[2] * TH + ph[2])
+        out[..., ch] = v
+    return np.clip(out, 0.05, 0.95).astype(np.float32)
