@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="tile edge: 16, 8, or 0 = autotuned with the blend depth")
     ap.add_argument("--blend-depth", type=int, default=0, help="records per blend batch (0 = tile^2)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-bg", action="store_true", help="skip the background-model measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--graph", type=int, default=-1,
@@ -411,6 +412,10 @@ def run_ours(args, ws_, rank, local):
     prof_steps = args.steps if graph is None else max(3, args.steps // 2)
     gpu_launches = int(round(sum(x[0] for x in prof.values()) / max(prof_steps, 1) * args.steps))
 
+    bg = None
+    if not args.no_bg and rank == 0:
+        bg = run_background(scene, tens, dev, stream, flush, peak, max(5, args.steps // 2))
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, scene, tens, cviews, opts, wsp, stream, dev, n_points, ws_, dist)
@@ -431,6 +436,7 @@ def run_ours(args, ws_, rank, local):
         "copies": w["D"], "needed_records": w["needed"],
         "autotune": tune,
         "roofline": roofline,
+        "background": bg,
         "blend_fwd_roofline": ({"achieved": blend["gbs"], "peak": peak, "unit": "GB/s",
                                 "frac": round((blend["gbs"] or 0) / peak, 4)} if blend else None),
         "kernels": kernels, "kernel_timing": prof_src, "gpu_launches": gpu_launches,
@@ -438,6 +444,65 @@ def run_ours(args, ws_, rank, local):
         "clocks": clocks, "e2e": e2e,
     }
     return out, dist
+
+
+def run_background(scene, tens, dev, stream, flush, peak, reps):
+    """Distilled background model on view 0 (Sec. 3.2): composite behind the
+    blend's output with a 1024 x 2048 x C spherical map and its backward (map
+    gradient, dL/dalpha), directions cached. Timed with CUDA events, L2 flushed
+    between repetitions. Algorithmic bytes: per pixel the image, alpha, cached
+    direction and output (fwd) or upstream gradient, alpha, direction and
+    dL/dalpha read+write (bwd); the map once; bwd also the fixed-point
+    accumulators (zeroed, read) and the map gradient."""
+    import torch
+
+    from paper_2508_19140_gb300 import rast, scenes
+
+    v = scene.views[0]
+    t = tens[0]
+    H, W, C = v.camera.height, v.camera.width, v.feat.shape[1]
+    env = torch.from_numpy(scenes.env_map(c=C)).to(dev)
+    e = rast.make_envmap(env)
+    cam = rast.make_camera(v.camera)
+    dirs = torch.empty((H, W, 3), device=dev)
+    rast.rasterize_view_dirs(cam, dirs, stream)
+    out = torch.empty((H, W, C), device=dev)
+    g = torch.randn((H, W, C), device=dev)
+    ga = torch.zeros((H, W), device=dev)
+    dmap = torch.empty_like(env)
+    scratch = torch.empty(rast.rasterize_bg_scratch_size(e), dtype=torch.uint8, device=dev)
+
+    def fwd():
+        rast.rasterize_bg_composite(cam, e, dirs, t["F"], t["A"], out, stream)
+
+    def bwd():
+        rast.rasterize_bg_composite_bwd(cam, e, dirs, t["A"], g, ga, dmap, scratch, stream)
+
+    res = {}
+    for name, fn in (("fwd", fwd), ("bwd", bwd)):
+        for _ in range(3):
+            fn()
+        evs = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        res[name] = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+    HW, M = H * W, env.numel()
+    b_fwd = HW * (4 * C + 4 + 12 + 4 * C) + 4 * M
+    b_bwd = HW * (4 * C + 4 + 12 + 8) + 4 * M + 8 * M * 2 + 4 * M
+    return {"what": "composite behind the blend with a 1024x2048xC spherical map (fwd) and its adjoint (bwd), "
+                    "view 0, cached directions",
+            "map": [int(env.shape[0]), int(env.shape[1]), C], "pixels": HW,
+            "fwd_ms": round(res["fwd"], 5), "bwd_ms": round(res["bwd"], 5),
+            "fwd_gbs": round(b_fwd / (res["fwd"] * 1e6), 1), "bwd_gbs": round(b_bwd / (res["bwd"] * 1e6), 1),
+            "fwd_frac": round(b_fwd / (res["fwd"] * 1e6) / peak, 4),
+            "bwd_frac": round(b_bwd / (res["bwd"] * 1e6) / peak, 4)}
 
 
 def run_e2e(args, scene, tens, cviews, opts, wsp, stream, dev, n_points, ws_, dist):

@@ -220,6 +220,58 @@ int32_t rasterize_profile_read(rast_profile_entry_t* out, int32_t max);
  * split, never the images (gradients agree to FP32 rounding). */
 int32_t rasterize_tune_candidates(int32_t mode, int32_t* tiles, int32_t* depths, int32_t max);
 
+/* ---------------------------------------------------------------------------
+ * Distilled background model (Sec. 3.2 "Faster Background Model Evaluation"):
+ * the background behind the points is a spherical environment map
+ * F_bg (H_b x W_b x C; the paper's is 1024 x 2048 x 4) read by bilinear
+ * interpolation along each pixel's viewing direction and composited with the
+ * transmittance the blend leaves (the T_{K+1} f_bg term of Eq. 2):
+ *     out = feat + (1 - alpha) * f_bg(d).
+ * Directions: d_c = ((x + 1/2 - cx) / fx, (y + 1/2 - cy) / fy, 1) normalised
+ * (camera space), rotated to world space with R^T. Map: longitude
+ * atan2(d_x, d_z) -> column (lambda / 2 pi + 1/2) W_b - 1/2, polar angle
+ * acos(d_y) -> row (theta / pi) H_b - 1/2; texel centres at integer + 1/2;
+ * columns wrap, rows clamp at the poles. All pointers are caller-owned device
+ * memory; calls are asynchronous on `stream`; argument errors return
+ * synchronously. ------------------------------------------------------------ */
+typedef struct {
+    const float* map;      /* [height][width][channels] FP32, row-major; 16-byte aligned
+                              when channels is a multiple of 4 */
+    int32_t height;        /* H_b (rows, polar angle) */
+    int32_t width;         /* W_b (columns, longitude) */
+    int32_t channels;      /* C: equal to the image's channels (1, 2, 3, 4, 8 or 16) */
+} rast_envmap_t;
+
+/* Camera-space unit viewing directions of every pixel ([height][width][3]
+ * FP32). They depend only on the intrinsics and the image size, so they can be
+ * computed once and passed to the calls below for every frame (the paper
+ * caches them). */
+rast_status_t rasterize_view_dirs(const rast_camera_t* cam, float* dirs, void* stream);
+
+/* out = feat + (1 - alpha) * f_bg for every pixel ([height][width][C]).
+ * `dirs`: cached directions from rasterize_view_dirs, or NULL to compute them
+ * from the intrinsics. `out` may equal `feat`. RAST_ERR_NOT_SUPPORTED for a
+ * channel count that is not compiled in. */
+rast_status_t rasterize_bg_composite(const rast_camera_t* cam, const rast_envmap_t* env, const float* dirs,
+                                     const float* feat, const float* alpha, float* out, void* stream);
+
+/* Bytes of device scratch rasterize_bg_composite_bwd needs (8 bytes per map
+ * element); 0 for an invalid map. */
+size_t rasterize_bg_scratch_size(const rast_envmap_t* env);
+
+/* Backward of rasterize_bg_composite for g = dL/dout ([height][width][C]):
+ *   g_alpha[p] += -(g[p] . f_bg[p])   (in place; NULL to skip; it is the
+ *                                      blend's dL/dalpha input),
+ *   d_map      = dL/dF_bg             ([H_b][W_b][C], overwritten),
+ * and dL/dfeat is g itself. The map gradient is summed as 64-bit fixed-point
+ * integers with resolution 2^-32 in `scratch` (rasterize_bg_scratch_size bytes,
+ * 8-byte aligned, contents overwritten), so it is bit-identical from run to run;
+ * each sum must stay below 2^31 in magnitude. RAST_ERR_CAPACITY if the scratch
+ * is too small. */
+rast_status_t rasterize_bg_composite_bwd(const rast_camera_t* cam, const rast_envmap_t* env, const float* dirs,
+                                         const float* alpha, const float* g, float* g_alpha, float* d_map,
+                                         void* scratch, size_t scratch_bytes, void* stream);
+
 /* Library version string. */
 const char* rasterize_version(void);
 

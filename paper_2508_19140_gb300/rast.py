@@ -82,6 +82,11 @@ class ProfileEntry(ct.Structure):
     _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int32), ("total_ms", ct.c_double)]
 
 
+class EnvMap(ct.Structure):
+    _fields_ = [("map", ct.c_void_p), ("height", ct.c_int32), ("width", ct.c_int32),
+                ("channels", ct.c_int32)]
+
+
 class WsEntry(ct.Structure):
     _fields_ = [("name", ct.c_char * 24), ("offset", ct.c_int64), ("bytes", ct.c_int64)]
 
@@ -104,6 +109,13 @@ SIGNATURES = {
                                                 ct.POINTER(WsEntry), ct.c_int32]),
     "rasterize_profile_enable": (None, [ct.c_int32]),
     "rasterize_profile_read": (ct.c_int32, [ct.POINTER(ProfileEntry), ct.c_int32]),
+    "rasterize_view_dirs": (ct.c_int, [ct.POINTER(Camera), ct.c_void_p, ct.c_void_p]),
+    "rasterize_bg_composite": (ct.c_int, [ct.POINTER(Camera), ct.POINTER(EnvMap), ct.c_void_p, ct.c_void_p,
+                                          ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "rasterize_bg_scratch_size": (ct.c_size_t, [ct.POINTER(EnvMap)]),
+    "rasterize_bg_composite_bwd": (ct.c_int, [ct.POINTER(Camera), ct.POINTER(EnvMap), ct.c_void_p, ct.c_void_p,
+                                              ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_size_t,
+                                              ct.c_void_p]),
     "rasterize_tune_candidates": (ct.c_int32, [ct.c_int32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
                                                ct.c_int32]),
     "rasterize_version": (ct.c_char_p, []),
@@ -294,6 +306,38 @@ def rasterize_profile_read() -> dict:
     n = L.rasterize_profile_read(ents, 64)
     return {ents[k].name.decode(): (int(ents[k].launches), float(ents[k].total_ms))
             for k in range(min(n, 64))}
+
+
+def make_envmap(env) -> EnvMap:
+    """env: device FP32 tensor [H_b, W_b, C] (contiguous)."""
+    e = EnvMap()
+    e.map = _ptr(env)
+    e.height, e.width, e.channels = int(env.shape[0]), int(env.shape[1]), int(env.shape[2])
+    return e
+
+
+def rasterize_view_dirs(camera: Camera, dirs, stream=None):
+    _check(load_library().rasterize_view_dirs(ct.byref(camera), _ptr(dirs), _stream(stream)),
+           "rasterize_view_dirs")
+
+
+def rasterize_bg_composite(camera: Camera, env: EnvMap, dirs, feat, alpha, out, stream=None):
+    _check(load_library().rasterize_bg_composite(ct.byref(camera), ct.byref(env), _ptr(dirs), _ptr(feat),
+                                                 _ptr(alpha), _ptr(out), _stream(stream)),
+           "rasterize_bg_composite")
+
+
+def rasterize_bg_scratch_size(env: EnvMap) -> int:
+    return int(load_library().rasterize_bg_scratch_size(ct.byref(env)))
+
+
+def rasterize_bg_composite_bwd(camera: Camera, env: EnvMap, dirs, alpha, g, g_alpha, d_map, scratch,
+                               stream=None):
+    _check(load_library().rasterize_bg_composite_bwd(ct.byref(camera), ct.byref(env), _ptr(dirs), _ptr(alpha),
+                                                     _ptr(g), _ptr(g_alpha), _ptr(d_map), _ptr(scratch),
+                                                     int(scratch.numel() * scratch.element_size()),
+                                                     _stream(stream)),
+           "rasterize_bg_composite_bwd")
 
 
 def rasterize_tune_candidates(mode="bilinear"):
