@@ -189,6 +189,24 @@ rast_status_t rasterize_batch(const rast_view_t* views, int32_t n_views, int32_t
                               const rast_opts_t* opts, void* workspace, size_t ws_bytes,
                               void* stream);
 
+/* Several point clouds rendered into ONE image (the ring buffer of
+ * view-specific clouds of Sec. 3.1 "Fast and Stable View-Specific Sampling
+ * during Inference": the clouds sampled for the last frames are reused and
+ * rendered together). The result is exactly that of one cloud holding
+ * clouds[0], clouds[1], ... concatenated in this order (equal depths fall
+ * back to that order), without copying them. clouds[k] and grads[k] are cloud
+ * k's points and point gradients (d_feat, d_opacity, d_xyz, d_scale); the
+ * image gradients g_feat, g_alpha, g_depth are taken from grads[0]; grads may
+ * be NULL for a forward-only pass. 1 <= n_clouds <= 16; same channel count and
+ * feature dtype in every cloud. Workspace, stream and errors as
+ * rasterize_batch; the workspace size comes from
+ * rasterize_clouds_workspace_size (0 for invalid arguments). */
+size_t rasterize_clouds_workspace_size(const rast_points_t* clouds, int32_t n_clouds, const rast_camera_t* cam,
+                                       const rast_opts_t* opts);
+rast_status_t rasterize_clouds(const rast_points_t* clouds, const rast_grads_t* grads, int32_t n_clouds,
+                               const rast_camera_t* cam, const rast_images_t* out, int32_t pass,
+                               const rast_opts_t* opts, void* workspace, size_t ws_bytes, void* stream);
+
 /* Synchronises `stream`, then reads the device-side status word and counters
  * of `workspace` (stats may be NULL). Returns the recorded status. */
 rast_status_t rasterize_get_status(const void* workspace, size_t ws_bytes, void* stream,

@@ -80,8 +80,10 @@ bool blend_depth_supported(int mode, int tile, int depth) {
     return depth == 2 * nt || (tile == 8 && depth == 4 * nt);
 }
 
+// cont[k] != 0: view k is another point cloud of view k - 1's image (same
+// camera, outputs and image gradients; its points join the same tile lists).
 rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_opts_t* o, int pass,
-                        Plan& pl) {
+                        Plan& pl, const uint8_t* cont = nullptr) {
     if (!views || !o || n_views < 1 || n_views > kMaxViews) return RAST_ERR_ARG;
     if (o->mode != RAST_SPLAT_BILINEAR && o->mode != RAST_SPLAT_GAUSSIAN) return RAST_ERR_ARG;
     if (o->gauss_cov != RAST_GAUSS_EWA && o->gauss_cov != RAST_GAUSS_ISO_SCREEN) return RAST_ERR_ARG;
@@ -114,9 +116,12 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     vt.rec_words = need <= 8 ? 8 : (need <= 16 ? 16 : 32);
     int64_t npt = 0, ntile = 0, npix = 0;
     uint32_t max_cull = 1;
+    int prim = 0;  // the view that owns the image of view k
     for (int k = 0; k < n_views; ++k) {
         const rast_view_t& v = views[k];
         if (v.pts.channels != C || v.pts.feat_dtype != dt) return RAST_ERR_ARG;
+        const bool joins = cont && cont[k] && k > 0;
+        if (!joins) prim = k;
         rast_status_t st = check_view(v, pass, o->tile);
         if (st != RAST_OK) return st;
         ViewDev& d = vt.v[k];
@@ -135,8 +140,8 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
         if (d.key_cull > max_cull) max_cull = d.key_cull;
         d.pt_off = npt;
         d.n = v.pts.n;
-        d.tile_off = ntile;
-        d.pix_off = npix;
+        d.tile_off = joins ? vt.v[prim].tile_off : ntile;
+        d.pix_off = joins ? vt.v[prim].pix_off : npix;
         d.xyz = v.pts.xyz;
         d.opacity = v.pts.opacity;
         d.feat = v.pts.feat;
@@ -151,9 +156,21 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
         d.d_opacity = v.grad.d_opacity;
         d.d_xyz = v.grad.d_xyz;
         d.d_scale = v.grad.d_scale;
+        if (joins) {
+            // Same image as the owning view: its outputs and image gradients.
+            const ViewDev& P = vt.v[prim];
+            d.out_feat = P.out_feat;
+            d.out_alpha = P.out_alpha;
+            d.out_depth = P.out_depth;
+            d.g_feat = P.g_feat;
+            d.g_alpha = P.g_alpha;
+            d.g_depth = P.g_depth;
+        }
         npt += v.pts.n;
-        ntile += (int64_t)d.tiles_x * d.tiles_y;
-        npix += (int64_t)c.width * c.height;
+        if (!joins) {
+            ntile += (int64_t)d.tiles_x * d.tiles_y;
+            npix += (int64_t)c.width * c.height;
+        }
     }
     if (npt >= ((int64_t)1 << 30) || ntile >= ((int64_t)1 << 30) || npix >= ((int64_t)1 << 40))
         return RAST_ERR_ARG;
@@ -399,6 +416,27 @@ rast_view_t single_view(const rast_points_t* pts, const rast_camera_t* cam, cons
     return v;
 }
 
+// One launch sequence over the views (cont: see make_plan).
+rast_status_t run_views(const rast_view_t* views, int32_t n_views, int32_t pass, const rast_opts_t* opts,
+                        void* workspace, size_t ws_bytes, void* stream, const uint8_t* cont) {
+    if (pass < 1 || pass > 3) return RAST_ERR_ARG;
+    Plan pl;
+    const rast_status_t st = make_plan(views, n_views, opts, pass, pl, cont);
+    if (st != RAST_OK) return st;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return RAST_ERR_ARG;
+    if (ws_bytes < pl.total) return RAST_ERR_CAPACITY;
+    Bufs b = make_bufs(pl, workspace);
+    if (make_record_map(pl.vt, b) != cudaSuccess) return RAST_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (pass & RAST_PASS_FWD) {
+        if (run_fwd(pl, b, s) != cudaSuccess) return RAST_ERR_CUDA;
+    }
+    if (pass & RAST_PASS_BWD) {
+        if (run_bwd(pl, b, s) != cudaSuccess) return RAST_ERR_CUDA;
+    }
+    return RAST_OK;
+}
+
 }  // namespace
 }  // namespace rast
 
@@ -457,23 +495,65 @@ int32_t rasterize_workspace_layout(const rast_view_t* views, int32_t n_views, co
 rast_status_t rasterize_batch(const rast_view_t* views, int32_t n_views, int32_t pass,
                               const rast_opts_t* opts, void* workspace, size_t ws_bytes,
                               void* stream) {
-    if (pass < 1 || pass > 3) return RAST_ERR_ARG;
-    Plan pl;
-    const rast_status_t st = make_plan(views, n_views, opts, pass, pl);
-    if (st != RAST_OK) return st;
-    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return RAST_ERR_ARG;
-    if (ws_bytes < pl.total) return RAST_ERR_CAPACITY;
-    Bufs b = make_bufs(pl, workspace);
-    if (make_record_map(pl.vt, b) != cudaSuccess) return RAST_ERR_CUDA;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (pass & RAST_PASS_FWD) {
-        if (run_fwd(pl, b, s) != cudaSuccess) return RAST_ERR_CUDA;
-    }
-    if (pass & RAST_PASS_BWD) {
-        if (run_bwd(pl, b, s) != cudaSuccess) return RAST_ERR_CUDA;
+    return run_views(views, n_views, pass, opts, workspace, ws_bytes, stream, nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Builds the view list of a multi-cloud image: cloud k becomes view k, views
+// 1.. join view 0's image.
+rast_status_t cloud_views(const rast_points_t* clouds, const rast_grads_t* grads, int32_t n_clouds,
+                          const rast_camera_t* cam, const rast_images_t* out, rast_view_t* views,
+                          uint8_t* cont) {
+    if (!clouds || !cam || !out || n_clouds < 1 || n_clouds > kMaxViews) return RAST_ERR_ARG;
+    for (int k = 0; k < n_clouds; ++k) {
+        std::memset(&views[k], 0, sizeof(rast_view_t));
+        views[k].pts = clouds[k];
+        views[k].cam = *cam;
+        views[k].out = *out;
+        if (grads) {
+            views[k].grad = grads[k];
+            views[k].grad.g_feat = grads[0].g_feat;
+            views[k].grad.g_alpha = grads[0].g_alpha;
+            views[k].grad.g_depth = grads[0].g_depth;
+        }
+        cont[k] = k > 0;
     }
     return RAST_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+size_t rasterize_clouds_workspace_size(const rast_points_t* clouds, int32_t n_clouds, const rast_camera_t* cam,
+                                       const rast_opts_t* opts) {
+    rast_view_t views[kMaxViews];
+    uint8_t cont[kMaxViews];
+    rast_images_t dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    if (cloud_views(clouds, nullptr, n_clouds, cam, &dummy, views, cont) != RAST_OK) return 0;
+    Plan pl;
+    if (make_plan(views, n_clouds, opts, 0, pl, cont) != RAST_OK) return 0;
+    return pl.total;
+}
+
+rast_status_t rasterize_clouds(const rast_points_t* clouds, const rast_grads_t* grads, int32_t n_clouds,
+                               const rast_camera_t* cam, const rast_images_t* out, int32_t pass,
+                               const rast_opts_t* opts, void* workspace, size_t ws_bytes, void* stream) {
+    rast_view_t views[kMaxViews];
+    uint8_t cont[kMaxViews];
+    if ((pass & RAST_PASS_BWD) && !grads) return RAST_ERR_ARG;
+    const rast_status_t st = cloud_views(clouds, grads, n_clouds, cam, out, views, cont);
+    if (st != RAST_OK) return st;
+    return run_views(views, n_clouds, pass, opts, workspace, ws_bytes, stream, cont);
+}
+
+}  // extern "C"
+
+extern "C" {
 
 rast_status_t rasterize_fwd(const rast_points_t* pts, const rast_camera_t* cam, const rast_opts_t* opts,
                             void* workspace, size_t ws_bytes, const rast_images_t* out, void* stream) {

@@ -109,6 +109,11 @@ SIGNATURES = {
                                                 ct.POINTER(WsEntry), ct.c_int32]),
     "rasterize_profile_enable": (None, [ct.c_int32]),
     "rasterize_profile_read": (ct.c_int32, [ct.POINTER(ProfileEntry), ct.c_int32]),
+    "rasterize_clouds_workspace_size": (ct.c_size_t, [ct.POINTER(Points), ct.c_int32, ct.POINTER(Camera),
+                                                      ct.POINTER(Opts)]),
+    "rasterize_clouds": (ct.c_int, [ct.POINTER(Points), ct.POINTER(Grads), ct.c_int32, ct.POINTER(Camera),
+                                    ct.POINTER(Images), ct.c_int32, ct.POINTER(Opts), ct.c_void_p, ct.c_size_t,
+                                    ct.c_void_p]),
     "rasterize_view_dirs": (ct.c_int, [ct.POINTER(Camera), ct.c_void_p, ct.c_void_p]),
     "rasterize_bg_composite": (ct.c_int, [ct.POINTER(Camera), ct.POINTER(EnvMap), ct.c_void_p, ct.c_void_p,
                                           ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -306,6 +311,25 @@ def rasterize_profile_read() -> dict:
     n = L.rasterize_profile_read(ents, 64)
     return {ents[k].name.decode(): (int(ents[k].launches), float(ents[k].total_ms))
             for k in range(min(n, 64))}
+
+
+def rasterize_clouds_workspace_size(clouds, camera: Camera, opts: Opts) -> int:
+    arr = (Points * len(clouds))(*clouds)
+    n = load_library().rasterize_clouds_workspace_size(arr, len(clouds), ct.byref(camera), ct.byref(opts))
+    if n == 0:
+        raise RastError(RAST_ERR_ARG, "rasterize_clouds_workspace_size")
+    return int(n)
+
+
+def rasterize_clouds(clouds, grads, camera: Camera, out: Images, pass_: int, opts: Opts, workspace,
+                     stream=None):
+    """clouds: list of Points; grads: list of Grads (one per cloud) or None."""
+    arr = (Points * len(clouds))(*clouds)
+    garr = None if grads is None else (Grads * len(grads))(*grads)
+    _check(load_library().rasterize_clouds(arr, garr, len(clouds), ct.byref(camera), ct.byref(out), int(pass_),
+                                           ct.byref(opts), _ptr(workspace),
+                                           int(workspace.numel() * workspace.element_size()), _stream(stream)),
+           "rasterize_clouds")
 
 
 def make_envmap(env) -> EnvMap:
