@@ -415,6 +415,9 @@ def run_ours(args, ws_, rank, local):
     bg = None
     if not args.no_bg and rank == 0:
         bg = run_background(scene, tens, dev, stream, flush, peak, max(5, args.steps // 2))
+    ring = None
+    if len(scene.views) == 1 and not do_bwd and rank == 0:
+        ring = run_ring(scene, tens, opts, dev, stream, flush, max(5, args.steps // 2), ms_step)
 
     e2e = None
     if not args.no_e2e:
@@ -437,6 +440,7 @@ def run_ours(args, ws_, rank, local):
         "autotune": tune,
         "roofline": roofline,
         "background": bg,
+        "ring_buffer": ring,
         "blend_fwd_roofline": ({"achieved": blend["gbs"], "peak": peak, "unit": "GB/s",
                                 "frac": round((blend["gbs"] or 0) / peak, 4)} if blend else None),
         "kernels": kernels, "kernel_timing": prof_src, "gpu_launches": gpu_launches,
@@ -503,6 +507,55 @@ def run_background(scene, tens, dev, stream, flush, peak, reps):
             "fwd_gbs": round(b_fwd / (res["fwd"] * 1e6), 1), "bwd_gbs": round(b_bwd / (res["bwd"] * 1e6), 1),
             "fwd_frac": round(b_fwd / (res["fwd"] * 1e6) / peak, 4),
             "bwd_frac": round(b_bwd / (res["bwd"] * 1e6) / peak, 4)}
+
+
+def run_ring(scene, tens, opts, dev, stream, flush, reps, ms_single):
+    """The inference frame's points as 4 view-specific clouds rendered into one
+    image with rasterize_clouds (Sec. 3.1 ring buffer), against the same points
+    as one cloud (the timed step) and against concatenating the 4 clouds into
+    one buffer first (the copy the multi-cloud call avoids)."""
+    import torch
+
+    from paper_2508_19140_gb300 import rast
+
+    v = scene.views[0]
+    t = tens[0]
+    n = v.xyz.shape[0]
+    cuts = [0, n // 4, n // 2, 3 * n // 4, n]
+    clouds = [rast.make_points(t["xyz"][a:b], t["op"][a:b], t["feat"][a:b],
+                               None if t.get("scale") is None else t["scale"][a:b])
+              for a, b in zip(cuts[:-1], cuts[1:])]
+    cam = rast.make_camera(v.camera)
+    ws = torch.empty(rast.rasterize_clouds_workspace_size(clouds, cam, opts), dtype=torch.uint8, device=dev)
+    out = rast.make_images(t["F"], t["A"], t["D"])
+    parts = [(t["xyz"][a:b].clone(), t["op"][a:b].clone(), t["feat"][a:b].clone()) for a, b in zip(cuts[:-1], cuts[1:])]
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        evs = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+
+    ms_clouds = timed(lambda: rast.rasterize_clouds(clouds, None, cam, out, rast.PASS_FWD, opts, ws, stream))
+
+    def concat():
+        for k in range(3):
+            torch.cat([p[k] for p in parts], out=(t["xyz"], t["op"], t["feat"])[k])
+    ms_cat = timed(concat)
+    return {"what": "the same points as 4 clouds in one rasterize_clouds call vs one cloud; concat_ms is the "
+                    "device copy that building one cloud from 4 would add",
+            "clouds": 4, "points": n, "ms_4_clouds": round(ms_clouds, 4), "ms_1_cloud": round(ms_single, 4),
+            "concat_ms": round(ms_cat, 4),
+            "points_per_s_4_clouds": round(n / (ms_clouds / 1e3), 1)}
 
 
 def run_e2e(args, scene, tens, cviews, opts, wsp, stream, dev, n_points, ws_, dist):
