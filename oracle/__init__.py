@@ -76,6 +76,8 @@ def lib():
             L.orc_env_composite.restype = None
             L.orc_env_backward.argtypes = [P, P, ct.c_int32, ct.c_int32, ct.c_int32, P, P, P, P, P]
             L.orc_env_backward.restype = None
+            L.orc_contract.argtypes = [ct.c_int64, P, P]
+            L.orc_contract.restype = None
             _lib = L
     return _lib
 
@@ -234,3 +236,11 @@ def env_backward(env, camera, alpha, g, dirs=None):
     lib().orc_env_backward(ct.byref(cam), _ptr(env), Hb, Wb, C, _ptr(dirs), _ptr(alpha), _ptr(g),
                            _ptr(d_alpha), _ptr(d_map))
     return d_alpha, d_map
+
+
+def contract(xyz):
+    """Spherical contraction x -> x (|x| <= 1) or (2 - 1/|x|) x/|x|, FP64."""
+    x = _f64(xyz).reshape(-1, 3)
+    out = np.zeros_like(x)
+    lib().orc_contract(x.shape[0], _ptr(x), _ptr(out))
+    return out

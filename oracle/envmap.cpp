@@ -1,4 +1,5 @@
-// CPU ORACLE for the distilled background model -- TEST INFRASTRUCTURE ONLY.
+// CPU ORACLE for the distilled background model and the spherical
+// contraction -- TEST INFRASTRUCTURE ONLY.
 //
 // Nothing in the product path may link, load or call this file (only the
 // tests, the package's smoke check and the benchmark's CPU baseline leg). It
@@ -138,3 +139,19 @@ void orc_env_backward(const orc_env_camera_t* cam, const double* map, int32_t Hb
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Spherical contraction of sampled positions (Sec. 3.4 "Implementation
+// Improvements": applied to the points before they enter the appearance field;
+// the contraction of Mip-NeRF 360): x if |x| <= 1, else (2 - 1/|x|) x / |x|.
+// FP64, one point at a time.
+extern "C" void orc_contract(int64_t n, const double* x, double* out) {
+    for (int64_t i = 0; i < n; ++i) {
+        const double a = x[3 * i], b = x[3 * i + 1], c = x[3 * i + 2];
+        const double r = std::sqrt(a * a + b * b + c * c);
+        const double s = r <= 1.0 ? 1.0 : (2.0 - 1.0 / r) / r;
+        out[3 * i] = s * a;
+        out[3 * i + 1] = s * b;
+        out[3 * i + 2] = s * c;
+    }
+}
