@@ -415,6 +415,9 @@ def run_ours(args, ws_, rank, local):
     bg = None
     if not args.no_bg and rank == 0:
         bg = run_background(scene, tens, dev, stream, flush, peak, max(5, args.steps // 2))
+    contraction = None
+    if not args.no_bg and rank == 0:
+        contraction = run_contract(tens, dev, stream, flush, peak, max(5, args.steps // 2))
     ring = None
     if len(scene.views) == 1 and not do_bwd and rank == 0:
         ring = run_ring(scene, tens, opts, dev, stream, flush, max(5, args.steps // 2), ms_step)
@@ -441,6 +444,7 @@ def run_ours(args, ws_, rank, local):
         "roofline": roofline,
         "background": bg,
         "ring_buffer": ring,
+        "contraction": contraction,
         "blend_fwd_roofline": ({"achieved": blend["gbs"], "peak": peak, "unit": "GB/s",
                                 "frac": round((blend["gbs"] or 0) / peak, 4)} if blend else None),
         "kernels": kernels, "kernel_timing": prof_src, "gpu_launches": gpu_launches,
@@ -507,6 +511,33 @@ def run_background(scene, tens, dev, stream, flush, peak, reps):
             "fwd_gbs": round(b_fwd / (res["fwd"] * 1e6), 1), "bwd_gbs": round(b_bwd / (res["bwd"] * 1e6), 1),
             "fwd_frac": round(b_fwd / (res["fwd"] * 1e6) / peak, 4),
             "bwd_frac": round(b_bwd / (res["bwd"] * 1e6) / peak, 4)}
+
+
+def run_contract(tens, dev, stream, flush, peak, reps):
+    """Fused spherical contraction (Sec. 3.4) of view 0's positions into a
+    separate buffer: 12 bytes read and 12 written per point."""
+    import torch
+
+    from paper_2508_19140_gb300 import rast
+
+    xyz = tens[0]["xyz"]
+    out = torch.empty_like(xyz)
+    for _ in range(3):
+        rast.rasterize_contract(xyz, out, stream)
+    evs = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rast.rasterize_contract(xyz, out, stream)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+    n = int(xyz.shape[0])
+    gbs = 24 * n / (ms * 1e6)
+    return {"points": n, "ms": round(ms, 5), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
 
 
 def run_ring(scene, tens, opts, dev, stream, flush, reps, ms_single):

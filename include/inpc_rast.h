@@ -290,6 +290,14 @@ rast_status_t rasterize_bg_composite_bwd(const rast_camera_t* cam, const rast_en
                                          const float* alpha, const float* g, float* g_alpha, float* d_map,
                                          void* scratch, size_t scratch_bytes, void* stream);
 
+/* Spherical contraction of n positions (Sec. 3.4 "Implementation
+ * Improvements"; the contraction of Mip-NeRF 360 that INPC applies to sampled
+ * points before its appearance field), in one kernel:
+ *     out_i = x_i                           if |x_i| <= 1
+ *           = (2 - 1/|x_i|) x_i / |x_i|     otherwise  (|out_i| < 2).
+ * xyz, out: device [n][3] FP32; out may equal xyz (in place). */
+rast_status_t rasterize_contract(const float* xyz, float* out, int64_t n, void* stream);
+
 /* Library version string. */
 const char* rasterize_version(void);
 

@@ -114,6 +114,7 @@ SIGNATURES = {
     "rasterize_clouds": (ct.c_int, [ct.POINTER(Points), ct.POINTER(Grads), ct.c_int32, ct.POINTER(Camera),
                                     ct.POINTER(Images), ct.c_int32, ct.POINTER(Opts), ct.c_void_p, ct.c_size_t,
                                     ct.c_void_p]),
+    "rasterize_contract": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p]),
     "rasterize_view_dirs": (ct.c_int, [ct.POINTER(Camera), ct.c_void_p, ct.c_void_p]),
     "rasterize_bg_composite": (ct.c_int, [ct.POINTER(Camera), ct.POINTER(EnvMap), ct.c_void_p, ct.c_void_p,
                                           ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -330,6 +331,12 @@ def rasterize_clouds(clouds, grads, camera: Camera, out: Images, pass_: int, opt
                                            ct.byref(opts), _ptr(workspace),
                                            int(workspace.numel() * workspace.element_size()), _stream(stream)),
            "rasterize_clouds")
+
+
+def rasterize_contract(xyz, out, stream=None):
+    """Spherical contraction of [n, 3] positions (out may be xyz)."""
+    _check(load_library().rasterize_contract(_ptr(xyz), _ptr(out), int(xyz.shape[0]), _stream(stream)),
+           "rasterize_contract")
 
 
 def make_envmap(env) -> EnvMap:
