@@ -208,7 +208,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
         pl.bytes[S_SSTATUS] = (size_t)(wa > wc ? wa : wc) * 4;
     }
     pl.bytes[S_RANGES] = (size_t)ntile * 8;
-    pl.bytes[S_ORDER] = (size_t)ntile * 4;
+    pl.bytes[S_ORDER] = (size_t)(ntile + 66) * 4;  // heavy-first order + bucket counts and cursors
     pl.bytes[S_CUTOFF] = (size_t)ntile * 8;
     pl.bytes[S_TRACE] = (size_t)ntile * 2 * 4 * 8;
     pl.bytes[S_TFINAL] = (size_t)npix * 4;

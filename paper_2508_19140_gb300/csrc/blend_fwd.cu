@@ -34,35 +34,55 @@
 namespace rast {
 namespace {
 
-// Tiles in descending order of list length, bucketed by floor(log2(len)).
-// One CTA; the order inside a bucket is arbitrary and only affects scheduling.
-__global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, int64_t P,
-                                                     uint32_t* __restrict__ order) {
+// Tiles in descending order of list length, bucketed by floor(log2(len)),
+// over the whole grid: k_tile_buckets counts the tiles of every bucket
+// (block-local counts, then one global add per bucket), k_tile_scatter turns
+// the 33 counts into bucket starts (heaviest bucket first) and places each
+// tile at its bucket's next free position. The order inside a bucket depends
+// on timing and only affects scheduling: every tile is blended the same way.
+__device__ __forceinline__ int len_bucket(uint2 r) {
+    const uint32_t len = r.y - r.x;
+    return len ? 32 - __clz(len) : 0;  // 0..32
+}
+
+__global__ void __launch_bounds__(256) k_tile_buckets(const uint2* __restrict__ ranges, int64_t P,
+                                                      uint32_t* __restrict__ counts) {
     __shared__ uint32_t s_cnt[33];
-    __shared__ uint32_t s_off[33];
     if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int64_t t = threadIdx.x; t < P; t += 1024) {
-        const uint2 r = ranges[t];
-        const uint32_t len = r.y - r.x;
-        const int bk = len ? 32 - __clz(len) : 0;  // 0..32
-        atomicAdd(&s_cnt[bk], 1u);
-    }
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P; t += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&s_cnt[len_bucket(ranges[t])], 1u);
     __syncthreads();
+    if (threadIdx.x < 33 && s_cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) k_tile_scatter(const uint2* __restrict__ ranges, int64_t P,
+                                                      const uint32_t* __restrict__ counts,
+                                                      uint32_t* __restrict__ cursor, uint32_t* __restrict__ order) {
+    __shared__ uint32_t s_start[33];  // global start of each bucket
+    __shared__ uint32_t s_cnt[33];    // this block's tiles per bucket, then its next free slot
     if (threadIdx.x == 0) {
         uint32_t run = 0;
         for (int bk = 32; bk >= 0; --bk) {
-            s_off[bk] = run;
-            run += s_cnt[bk];
+            s_start[bk] = run;
+            run += counts[bk];
         }
     }
+    if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int64_t t = threadIdx.x; t < P; t += 1024) {
-        const uint2 r = ranges[t];
-        const uint32_t len = r.y - r.x;
-        const int bk = len ? 32 - __clz(len) : 0;
-        order[atomicAdd(&s_off[bk], 1u)] = (uint32_t)t;
+    // This block's contiguous chunk of tiles: count, reserve one range per
+    // bucket with a single global atomic, then place.
+    const int64_t chunk = (P + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = lo + chunk < P ? lo + chunk : P;
+    for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) atomicAdd(&s_cnt[len_bucket(ranges[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x < 33) {
+        const uint32_t c = s_cnt[threadIdx.x];
+        s_cnt[threadIdx.x] = s_start[threadIdx.x] + (c ? atomicAdd(&cursor[threadIdx.x], c) : 0u);
     }
+    __syncthreads();
+    for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x)
+        order[atomicAdd(&s_cnt[len_bucket(ranges[t])], 1u)] = (uint32_t)t;
 }
 
 // cp.async ring depth (batches in flight per CTA): three batches of one record
@@ -448,9 +468,21 @@ bool channels_supported(int C) {
 }
 
 cudaError_t launch_tile_order(const ViewTable& vt, const Bufs& b, cudaStream_t s) {
-    if (vt.tiles_total == 0) return cudaSuccess;
-    ProfScope ps("tile_order", s);
-    k_tile_order<<<1, 1024, 0, s>>>(b.ranges, vt.tiles_total, b.order);
+    const int64_t P = vt.tiles_total;
+    if (P == 0) return cudaSuccess;
+    uint32_t* counts = b.order + P;  // 33 bucket counts, then 33 cursors
+    cudaError_t e = cudaMemsetAsync(counts, 0, 66 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const int64_t want = (P + 255) / 256;
+    const unsigned grid = (unsigned)(want < 1024 ? want : 1024);
+    {
+        ProfScope ps("tile_order.count", s);
+        k_tile_buckets<<<grid, 256, 0, s>>>(b.ranges, P, counts);
+    }
+    {
+        ProfScope ps("tile_order.scatter", s);
+        k_tile_scatter<<<grid, 256, 0, s>>>(b.ranges, P, counts, counts + 33, b.order);
+    }
     return cudaGetLastError();
 }
 

@@ -45,6 +45,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp
 
 constexpr int kT = 256;
 constexpr int kPer = kScanItems / kT;  // 4 consecutive items per thread
+static_assert(kPer == 4, "the scans load four items per thread");
 
 // Sorted-order rects of a block of kScanItems points (gathered once, kept for
 // k_dup_write) and the block's copy count.
@@ -82,25 +83,28 @@ __global__ void __launch_bounds__(kT) k_dup_count(const uint32_t* __restrict__ s
     if (threadIdx.x == 0) blk[blockIdx.x] = tot;
 }
 
+// Four consecutive counts per thread (one 16-byte load when in range).
+__device__ __forceinline__ void load4(const uint32_t* __restrict__ p, int64_t s0, int64_t n, uint32_t v[4]) {
+    if (s0 + 4 <= n) {
+        const uint4 q = *reinterpret_cast<const uint4*>(p + s0);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = s0 + j < n ? p[s0 + j] : 0u;
+    }
+}
+
 __global__ void __launch_bounds__(kT) k_count_blocks(const uint32_t* __restrict__ cnt, int64_t n,
                                                      uint32_t* __restrict__ blk) {
     __shared__ uint32_t s_warp[33];
-    const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
-    uint32_t c = 0;
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        const int64_t s = b0 + j * kT + threadIdx.x;
-        if (s < n) c += cnt[s];
-    }
+    const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
+    uint32_t v[kPer];
+    load4(cnt, s0, n, v);
     uint32_t tot;
-    block_excl_scan<kT>(c, s_warp, tot);
+    block_excl_scan<kT>(v[0] + v[1] + v[2] + v[3], s_warp, tot);
     if (threadIdx.x == 0) blk[blockIdx.x] = tot;
 }
 
-// Exclusive scan of nb block sums in place (one block). If hdr is given the
-// total is the copy count D, summed in 64 bits: if it exceeds the capacity the
-// capacity bit is raised and D is published as 0, so every later stage sees an
-// empty copy list instead of a truncated one.
 __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ blk, int64_t nb,
                                                       WsHeader* hdr, int64_t cap) {
     __shared__ uint32_t s_warp[33];
@@ -187,20 +191,26 @@ __global__ void __launch_bounds__(kT) k_scan_apply(const uint32_t* __restrict__ 
                                                    const uint32_t* __restrict__ blk,
                                                    uint32_t* __restrict__ base) {
     __shared__ uint32_t s_warp[33];
-    const int64_t b0 = (int64_t)blockIdx.x * kScanItems;
-    uint32_t off = blk[blockIdx.x];
-#pragma unroll 1
+    const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
+    uint32_t v[kPer];
+    load4(cnt, s0, n, v);
+    uint32_t tot;
+    uint32_t o = blk[blockIdx.x] + block_excl_scan<kT>(v[0] + v[1] + v[2] + v[3], s_warp, tot);
+    uint32_t r[kPer];
+#pragma unroll
     for (int j = 0; j < kPer; ++j) {
-        const int64_t s = b0 + j * kT + threadIdx.x;
-        const uint32_t c = s < n ? cnt[s] : 0u;
-        uint32_t tot;
-        const uint32_t o = off + block_excl_scan<kT>(c, s_warp, tot);
-        off += tot;
-        if (s < n) base[s] = o;
+        r[j] = o;
+        o += v[j];
+    }
+    if (s0 + kPer <= n) {
+        *reinterpret_cast<uint4*>(base + s0) = make_uint4(r[0], r[1], r[2], r[3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j)
+            if (s0 + j < n) base[s0 + j] = r[j];
     }
 }
 
-// Tile ranges [start, end) from the tile-sorted keys (ranges pre-zeroed).
 __global__ void __launch_bounds__(kT) k_ranges(const uint32_t* __restrict__ keys,
                                                const WsHeader* __restrict__ hdr,
                                                uint2* __restrict__ ranges) {
