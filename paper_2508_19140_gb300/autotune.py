@@ -68,11 +68,14 @@ def tune_key(device_name: str, opts, cviews, passes: int) -> str:
             f"|px2^{_bucket(px)}|pts2^{_bucket(pts)}")
 
 
-def select(timings: dict) -> tuple:
-    """Fastest (tile, depth); ties go to the earlier candidate (the default)."""
+def select(timings: dict, margin: float = 0.02) -> tuple:
+    """Fastest (tile, depth), where a later candidate must beat the best
+    earlier one by more than `margin` (relative): near-ties, which run-to-run
+    noise would otherwise decide, go to the earlier candidate (the default
+    first), so the choice is stable."""
     best, best_ms = None, math.inf
     for cand, ms in timings.items():
-        if ms is not None and ms < best_ms:
+        if ms is not None and ms < best_ms * (1.0 - margin):
             best, best_ms = cand, ms
     return best
 
