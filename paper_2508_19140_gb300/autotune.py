@@ -68,7 +68,7 @@ def tune_key(device_name: str, opts, cviews, passes: int) -> str:
             f"|px2^{_bucket(px)}|pts2^{_bucket(pts)}")
 
 
-def select(timings: dict, margin: float = 0.02) -> tuple:
+def select(timings: dict, margin: float = 0.01) -> tuple:
     """Fastest (tile, depth), where a later candidate must beat the best
     earlier one by more than `margin` (relative): near-ties, which run-to-run
     noise would otherwise decide, go to the earlier candidate (the default

@@ -48,7 +48,7 @@ constexpr int stages_for() { return RPT == 1 ? 3 : 2; }
 template <int TS, int RPT, int C, bool BF16>
 constexpr size_t bilinear_bwd_smem() {
     constexpr int D = TS * TS * RPT;
-    return sizeof(uint32_t) * stages_for<RPT>() * D * RecLayout<0, C, BF16>::words  // record ring
+    return sizeof(uint32_t) * stages_for<RPT>() * D * ring_stride(RecLayout<0, C, BF16>::words)  // record ring
            + sizeof(float) * 4 * 2 * D                                              // (T a, w dL/da) per slot
            + sizeof(float) * TS * TS * C                                            // upstream dL/dF per pixel
            + 128;
@@ -72,16 +72,18 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
     constexpr int PS = partial_stride(P);
     constexpr int GS = grow_stride(P);
     constexpr int RW = RecLayout<0, C, BF16>::words;
+    constexpr int RS = ring_stride(RW);
     constexpr int FW = RecLayout<0, C, BF16>::feat_word;
     extern __shared__ __align__(128) uint32_t s_dyn[];
-    uint32_t* const s_ring = align128(s_dyn);                                 // [kStages][D][RW]
-    float* const s_ta = reinterpret_cast<float*>(s_ring + kStages * D * RW);  // [4][D]
+    uint32_t* const s_ring = align128(s_dyn);                                 // [kStages][D][RS]
+    float* const s_ta = reinterpret_cast<float*>(s_ring + kStages * D * RS);  // [4][D]
     float* const s_da = s_ta + 4 * D;                                         // [4][D]
     float* const s_gF = s_da + 4 * D;                                         // [NT][C]
     __shared__ uint32_t s_mask[NT][MW + 1];
     __shared__ float s_w[4][D];    // bilinear weight per slot
     __shared__ float s_inv[4][D];  // 1 / (1 - alpha) per slot
     __shared__ float s_o[D];       // opacity per record
+    __shared__ float s_z[D];       // depth per record
     __shared__ uint32_t s_anchor[D];
     __shared__ uint32_t s_red;
 
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (gi[k] != 0xffffffffu) {
-                uint32_t* dst = s_ring + ((size_t)st * D + k * NT + tid) * RW;
+                uint32_t* dst = s_ring + ((size_t)st * D + k * NT + tid) * RS;
                 const uint32_t* src = rec + (size_t)gi[k] * RW;
 #pragma unroll
                 for (int q = 0; q < RW; q += 4) cp_async16(dst + q, src + q);
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
     for (uint32_t j = 0; j < nb; ++j) {
         const uint32_t bi = nb - 1 - j;
         const int st = (int)(j % kStages);
-        const uint32_t* ring = s_ring + (size_t)st * D * RW;
+        const uint32_t* ring = s_ring + (size_t)st * D * RS;
         const uint32_t rel0 = bi * D;
 #pragma unroll
         for (int k = 0; k < 4 * RPT; ++k) {
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
             const int r = k * NT + tid;
             const uint32_t q = rg.x + rel0 + r;
             if (q >= end) continue;
-            const uint4 g = *reinterpret_cast<const uint4*>(ring + r * RW);
+            const uint4 g = *reinterpret_cast<const uint4*>(ring + r * RS);
             const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
             const float o = __uint_as_float(g.w);
             const float ax = __fsub_rn(1.f, bg.a), by = __fsub_rn(1.f, bg.b);
@@ -200,6 +202,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
             const float w2 = __fmul_rn(ax, bg.b), w3 = __fmul_rn(bg.a, bg.b);
             s_w[0][r] = w0; s_w[1][r] = w1; s_w[2][r] = w2; s_w[3][r] = w3;
             s_o[r] = o;
+            s_z[r] = __uint_as_float(g.z);
             // 1 / (1 - alpha) of each slot, alpha = min(o w, amax) exactly as the forward has it
             s_inv[0][r] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w0), amax)));
             s_inv[1][r] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w1), amax)));
@@ -255,13 +258,13 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
                 const float alpha = fminf(ow, amax);
                 const float inv = s_inv[slot][r];
                 const float Tk = T * inv;  // T_k = T_{k+1} / (1 - alpha_k)
-                const uint32_t* rp = ring + r * RW;
+                const uint32_t* rp = ring + r * RS;
                 float f[C];
                 load_features<C, BF16>(rp + FW, f);
                 float fdot = 0.f;
 #pragma unroll
                 for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], f[c], fdot);
-                const float z = __uint_as_float(rp[2]);
+                const float z = s_z[r];
                 const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) * inv;
                 const float ta = Tk * alpha;
                 Sg = fmaf(ta, fdot, Sg);

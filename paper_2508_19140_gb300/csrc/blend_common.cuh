@@ -116,6 +116,13 @@ struct RecLayout {
     static constexpr int words = need <= 8 ? 8 : (need <= 16 ? 16 : 32);
 };
 
+// Shared-memory stride (words) of a staged record: 4 words more than its
+// global stride, so consecutive records start in 8 different 4-bank groups
+// (a stride of 8, 16 or 32 words would start them in at most 4) and the
+// per-fragment reads of random records conflict less; still a multiple of 16
+// bytes for cp.async.
+__host__ __device__ constexpr int ring_stride(int rw) { return rw + 4; }
+
 // 128-byte aligned view of a dynamic shared-memory buffer (allocated with
 // 128 spare bytes).
 __device__ __forceinline__ uint32_t* align128(uint32_t* p) {

@@ -92,7 +92,7 @@ constexpr int stages_for() { return RPT == 1 ? 3 : 2; }
 
 template <int TS, int RPT, int C, bool BF16>
 constexpr size_t bilinear_fwd_smem() {
-    return sizeof(uint32_t) * stages_for<RPT>() * TS * TS * RPT * RecLayout<0, C, BF16>::words + 128;
+    return sizeof(uint32_t) * stages_for<RPT>() * TS * TS * RPT * ring_stride(RecLayout<0, C, BF16>::words) + 128;
 }
 
 // RPT = records each thread stages per batch: the batch ("blend depth") is
@@ -111,12 +111,14 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     const unsigned long long t_start = global_ns();
     const long long c_start = clock64();
     constexpr int RW = RecLayout<0, C, BF16>::words;
+    constexpr int RS = ring_stride(RW);
     constexpr int FW = RecLayout<0, C, BF16>::feat_word;
     extern __shared__ __align__(128) uint32_t s_dyn[];
-    uint32_t* const s_ring = align128(s_dyn);  // [kStages][D][RW] raw records
+    uint32_t* const s_ring = align128(s_dyn);  // [kStages][D][RS] raw records
     __shared__ uint32_t s_mask[NT][MW + 1];    // MW words + 1 pad: conflict-free row reads
     __shared__ float s_alpha[4][D];            // alpha of each record's 2x2 slots (FP32, pinned ops)
     __shared__ uint32_t s_anchor[D];           // tile-local anchor (X0 + 1) | (Y0 + 1) << 8
+    __shared__ float s_z[D];                   // depth per record (one word per bank-spread slot)
     __shared__ uint32_t s_maxstop;
 
     const int64_t tile = order[blockIdx.x];
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (gi[k] != 0xffffffffu) {
-                uint32_t* dst = s_ring + ((size_t)(j % kStages) * D + k * NT + tid) * RW;
+                uint32_t* dst = s_ring + ((size_t)(j % kStages) * D + k * NT + tid) * RS;
                 const uint32_t* src = rec + (size_t)gi[k] * RW;
 #pragma unroll
                 for (int q = 0; q < RW; q += 4) cp_async16(dst + q, src + q);
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     }
 
     for (uint32_t j = 0; j < nbatch; ++j) {
-        const uint32_t* ring = s_ring + (size_t)(j % kStages) * D * RW;
+        const uint32_t* ring = s_ring + (size_t)(j % kStages) * D * RS;
         cp_async_wait<kStages - 1>();  // this thread's copies of batch j have landed
         const uint32_t rel0 = j * D;
 #pragma unroll
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
                 // Per record: the four fragment alphas of its 2x2 box (the ops of
                 // bilin_weight and the clamp, so every pixel sees the same FP32
                 // bits) and one mask bit per covered pixel of this tile.
-                const uint4 g = *reinterpret_cast<const uint4*>(ring + r * RW);
+                const uint4 g = *reinterpret_cast<const uint4*>(ring + r * RS);
                 const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
                 const float o = __uint_as_float(g.w);
                 const float ax = __fsub_rn(1.f, bg.a), by = __fsub_rn(1.f, bg.b);
@@ -197,6 +199,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
                 s_alpha[3][r] = fminf(__fmul_rn(o, __fmul_rn(bg.a, bg.b)), amax);
                 const int X0 = bg.i0 - tx * TS, Y0 = bg.j0 - ty * TS;
                 s_anchor[r] = (uint32_t)(X0 + 1) | ((uint32_t)(Y0 + 1) << 8);
+                s_z[r] = __uint_as_float(g.z);
                 const uint32_t bit = 1u << lane;
                 const int word = r >> 5;
 #pragma unroll
@@ -231,13 +234,13 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
                     stop = rel0 + r + 1;
                     break;
                 }
-                const uint32_t* rp = ring + r * RW;
+                const uint32_t* rp = ring + r * RS;
                 float f[C];
                 load_features<C, BF16>(rp + FW, f);
                 const float ta = T * alpha;
 #pragma unroll
                 for (int c = 0; c < C; ++c) F[c] = fmaf(ta, f[c], F[c]);
-                Dp = fmaf(ta, __uint_as_float(rp[2]), Dp);
+                Dp = fmaf(ta, s_z[r], Dp);
                 A += ta;
                 T = nT;
                 last = rel0 + r + 1;

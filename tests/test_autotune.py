@@ -43,7 +43,7 @@ def test_candidates_from_library(lib):
 def test_select_min_and_ties_to_default():
     assert autotune.select({(16, 256): 3.0, (8, 64): 2.0, (8, 128): 2.5}) == (8, 64)
     assert autotune.select({(16, 256): 2.0, (8, 64): 2.0}) == (16, 256)
-    assert autotune.select({(16, 256): 2.0, (8, 64): 1.99}) == (16, 256)   # within 2 %: keep the earlier
+    assert autotune.select({(16, 256): 2.0, (8, 64): 1.99}) == (16, 256)   # within 1 %: keep the earlier
     assert autotune.select({(16, 256): 2.0, (8, 64): 1.9}) == (8, 64)
     assert autotune.select({(16, 256): None, (8, 64): 4.0}) == (8, 64)
     assert autotune.select({(16, 256): None}) is None
