@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
 // ---------------------------------------------------------------- K8 reduce
 
 template <int C, int MODE>
-__global__ void __launch_bounds__(256) k_reduce_grads(const ViewTable vt, const uint32_t* __restrict__ zbits,
+__global__ void __launch_bounds__(256, 6) k_reduce_grads(const ViewTable vt, const uint32_t* __restrict__ zbits,
                                                       const uint2* __restrict__ rect,
                                                       const uint32_t* __restrict__ base,
                                                       const uint2* __restrict__ cutoff,

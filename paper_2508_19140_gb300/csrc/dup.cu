@@ -215,10 +215,27 @@ __global__ void __launch_bounds__(kT) k_ranges(const uint32_t* __restrict__ keys
                                                const WsHeader* __restrict__ hdr,
                                                uint2* __restrict__ ranges) {
     const int64_t D = hdr->n_copies;
-    for (int64_t p = (int64_t)blockIdx.x * kT + threadIdx.x; p < D; p += (int64_t)gridDim.x * kT) {
-        const uint32_t t = keys[p];
-        if (p == 0 || keys[p - 1] != t) ranges[t].x = (uint32_t)p;
-        if (p + 1 == D || keys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+    // Four consecutive keys per thread (one 16-byte load) plus the keys just
+    // before and after them; a range starts or ends where neighbours differ.
+    for (int64_t p0 = ((int64_t)blockIdx.x * kT + threadIdx.x) * 4; p0 < D; p0 += (int64_t)gridDim.x * kT * 4) {
+        uint32_t k[6];  // keys p0-1 .. p0+4 (sentinels outside [0, D))
+        k[0] = p0 > 0 ? keys[p0 - 1] : 0xffffffffu;
+        if (p0 + 4 <= D) {
+            const uint4 q = *reinterpret_cast<const uint4*>(keys + p0);
+            k[1] = q.x; k[2] = q.y; k[3] = q.z; k[4] = q.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) k[1 + j] = p0 + j < D ? keys[p0 + j] : 0xffffffffu;
+        }
+        k[5] = p0 + 4 < D ? keys[p0 + 4] : 0xffffffffu;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t p = p0 + j;
+            if (p >= D) break;
+            const uint32_t t = k[1 + j];
+            if (p == 0 || k[j] != t) ranges[t].x = (uint32_t)p;
+            if (p + 1 == D || k[2 + j] != t) ranges[t].y = (uint32_t)(p + 1);
+        }
     }
 }
 
