@@ -40,15 +40,17 @@ __device__ __forceinline__ uint32_t block_max_u32(uint32_t x, uint32_t* s) {
 
 // ---------------------------------------------------------------- bilinear
 
-// cp.async ring depth (batches in flight per CTA): three batches of one record
-// per thread, two of deeper batches.
-template <int RPT>
-constexpr int stages_for() { return RPT == 1 ? 3 : 2; }
+// cp.async ring depth (batches in flight per CTA): three batches for 16x16
+// tiles with one record per thread; two otherwise (deeper batches hide more
+// latency each, and 8x8 tiles gain more from the extra CTAs per SM that a
+// smaller ring leaves room for).
+template <int TS, int RPT>
+constexpr int stages_for() { return TS == 16 && RPT == 1 ? 3 : 2; }
 
 template <int TS, int RPT, int C, bool BF16>
 constexpr size_t bilinear_bwd_smem() {
     constexpr int D = TS * TS * RPT;
-    return sizeof(uint32_t) * stages_for<RPT>() * D * ring_stride(RecLayout<0, C, BF16>::words)  // record ring
+    return sizeof(uint32_t) * stages_for<TS, RPT>() * D * ring_stride(RecLayout<0, C, BF16>::words)  // record ring
            + sizeof(float) * 4 * 2 * D                                              // (T a, w dL/da) per slot
            + sizeof(float) * TS * TS * C                                            // upstream dL/dF per pixel
            + 128;
@@ -65,7 +67,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
     constexpr int NT = TS * TS;  // threads = pixels
     constexpr int D = NT * RPT;  // records per batch
     constexpr int MW = D / 32;   // mask words per pixel
-    constexpr int kStages = stages_for<RPT>();
+    constexpr int kStages = stages_for<TS, RPT>();
     const unsigned long long t_start = global_ns();
     const long long c_start = clock64();
     constexpr int P = C + 1;  // dfeat[C], dopacity

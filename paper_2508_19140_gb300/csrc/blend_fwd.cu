@@ -85,14 +85,16 @@ __global__ void __launch_bounds__(256) k_tile_scatter(const uint2* __restrict__ 
         order[atomicAdd(&s_cnt[len_bucket(ranges[t])], 1u)] = (uint32_t)t;
 }
 
-// cp.async ring depth (batches in flight per CTA): three batches of one record
-// per thread, two of deeper batches.
-template <int RPT>
-constexpr int stages_for() { return RPT == 1 ? 3 : 2; }
+// cp.async ring depth (batches in flight per CTA): three batches for 16x16
+// tiles with one record per thread; two otherwise (deeper batches hide more
+// latency each, and 8x8 tiles gain more from the extra CTAs per SM that a
+// smaller ring leaves room for).
+template <int TS, int RPT>
+constexpr int stages_for() { return TS == 16 && RPT == 1 ? 3 : 2; }
 
 template <int TS, int RPT, int C, bool BF16>
 constexpr size_t bilinear_fwd_smem() {
-    return sizeof(uint32_t) * stages_for<RPT>() * TS * TS * RPT * ring_stride(RecLayout<0, C, BF16>::words) + 128;
+    return sizeof(uint32_t) * stages_for<TS, RPT>() * TS * TS * RPT * ring_stride(RecLayout<0, C, BF16>::words) + 128;
 }
 
 // RPT = records each thread stages per batch: the batch ("blend depth") is
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     constexpr int NT = TS * TS;     // threads = pixels
     constexpr int D = NT * RPT;     // records per batch
     constexpr int MW = D / 32;      // mask words per pixel
-    constexpr int kStages = stages_for<RPT>();
+    constexpr int kStages = stages_for<TS, RPT>();
     const unsigned long long t_start = global_ns();
     const long long c_start = clock64();
     constexpr int RW = RecLayout<0, C, BF16>::words;
