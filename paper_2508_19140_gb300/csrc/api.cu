@@ -222,39 +222,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     return RAST_OK;
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_tiled_fn() {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
 }  // namespace
-
-cudaError_t make_record_map(const ViewTable& vt, Bufs& b) {
-    EncodeTiledFn enc = encode_tiled_fn();
-    if (!enc) return cudaErrorNotSupported;
-    const cuuint64_t dims[2] = {(cuuint64_t)vt.rec_words, (cuuint64_t)(vt.n_total > 0 ? vt.n_total : 1)};
-    const cuuint64_t strides[1] = {(cuuint64_t)vt.rec_words * 4};
-    const cuuint32_t box[2] = {(cuuint32_t)vt.rec_words, 1};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = enc(&b.rec_map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, b.rec, dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
 
 namespace {
 
@@ -426,7 +394,6 @@ rast_status_t run_views(const rast_view_t* views, int32_t n_views, int32_t pass,
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return RAST_ERR_ARG;
     if (ws_bytes < pl.total) return RAST_ERR_CAPACITY;
     Bufs b = make_bufs(pl, workspace);
-    if (make_record_map(pl.vt, b) != cudaSuccess) return RAST_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (pass & RAST_PASS_FWD) {
         if (run_fwd(pl, b, s) != cudaSuccess) return RAST_ERR_CUDA;

@@ -14,71 +14,12 @@
 //              once T' < t_min.
 #pragma once
 
-#include <cuda.h>
-
 #include "rast_internal.cuh"
 
 namespace rast {
 
-// ---- TMA gather staging ----------------------------------------------------
-// Records are rows of a 2D tensor [n_points][rec_words] (u32). One
-// cp.async.bulk.tensor ... tile::gather4 brings four rows (any four point
-// indices) into four consecutive shared-memory rows and signals an mbarrier
-// with the byte count (complete_tx). The tensor map's box is one row high.
-
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// Orders this thread's view of earlier generic-proxy shared-memory accesses
-// (made visible to it by a barrier) before its later async-proxy (TMA) writes.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for phase `parity` of `bar`: false after ~2^22 polls (each
-// try_wait suspends the thread for a while), i.e. seconds, far beyond any
-// legitimate copy latency.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-#pragma unroll 1
-    for (uint32_t it = 0; it < (1u << 22); ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void tma_gather4(void* dst, const CUtensorMap* map, int col, int r0, int r1,
-                                            int r2, int r3, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(col), "r"(r0), "r"(r1), "r"(r2), "r"(r3),
-        "r"(smem_addr(bar))
-        : "memory");
 }
 
 // ---- cp.async (LDGSTS) staging ----------------------------------------------
@@ -105,9 +46,8 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Record stride (u32 words) for a mode, channel count and feature type; the
 // host computes the same value (rec_words). A power of two of at least 8
-// words (32 bytes): a gather4 group of four rows is then a multiple of 128
-// bytes, so every group lands 128-byte aligned in shared memory, and no
-// record straddles a 64-byte DRAM burst.
+// words (32 bytes): every record is 16-byte aligned for cp.async and no record
+// straddles a 64-byte DRAM burst, so each gather costs one burst.
 template <int MODE, int C, bool BF16>
 struct RecLayout {
     static constexpr int feat_word = MODE == 0 ? 4 : 8;

@@ -2,7 +2,6 @@
 // Shared by the kernel translation units and the C-ABI layer in api.cu.
 #pragma once
 
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -182,7 +181,6 @@ struct Bufs {
     float* t_final;
     uint32_t* last;
     WsHeader* hdr;
-    CUtensorMap rec_map;  // records as a [n_points][rec_words] u32 tensor, one-row boxes (TMA gather4)
     int64_t copy_cap;
     int64_t blk_cap;
 };
@@ -230,8 +228,6 @@ cudaError_t launch_reduce_grads(const ViewTable& vt, const Bufs& b, cudaStream_t
 
 bool channels_supported(int C);
 
-// Encodes b.rec_map for the records array (host; needs the driver entry point).
-cudaError_t make_record_map(const ViewTable& vt, Bufs& b);
 
 constexpr int kScanItems = 1024;   // items per block in the dup / point scans
 
