@@ -418,6 +418,9 @@ def run_ours(args, ws_, rank, local):
     contraction = None
     if not args.no_bg and rank == 0:
         contraction = run_contract(tens, dev, stream, flush, peak, max(5, args.steps // 2))
+    untiled = None
+    if len(scene.views) == 1 and scene.mode == "bilinear" and not args.no_bg and rank == 0:
+        untiled = run_untiled(scene, tens, dev, stream, flush, max(5, args.steps // 2))
     ring = None
     if len(scene.views) == 1 and not do_bwd and rank == 0:
         ring = run_ring(scene, tens, opts, dev, stream, flush, max(5, args.steps // 2), ms_step)
@@ -444,6 +447,7 @@ def run_ours(args, ws_, rank, local):
         "roofline": roofline,
         "background": bg,
         "ring_buffer": ring,
+        "untiled_baseline": untiled,
         "contraction": contraction,
         "blend_fwd_roofline": ({"achieved": blend["gbs"], "peak": peak, "unit": "GB/s",
                                 "frac": round((blend["gbs"] or 0) / peak, 4)} if blend else None),
@@ -538,6 +542,64 @@ def run_contract(tens, dev, stream, flush, peak, reps):
     n = int(xyz.shape[0])
     gbs = 24 * n / (ms * 1e6)
     return {"points": n, "ms": round(ms, 5), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+
+
+def run_untiled(scene, tens, dev, stream, flush, reps):
+    """Forward of the same frame with the untiled baseline (per-pixel lists,
+    ~4 copies per point, one thread per pixel) against the tiled forward at
+    16x16 and 8x8 tiles, with the per-kernel split of the untiled run: what
+    tiling saves on this GPU (Sec. 3.2 "Tiled Rendering")."""
+    import torch
+
+    from paper_2508_19140_gb300 import rast
+
+    t = tens[0]
+    v = scene.views[0]
+    pts = rast.make_points(t["xyz"], t["op"], t["feat"])
+    cam = rast.make_camera(v.camera)
+    out = rast.make_images(t["F"], t["A"], t["D"])
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        evs = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+
+    res = {}
+    o_u = rast.make_opts(mode="bilinear")
+    ws_u = torch.empty(rast.rasterize_untiled_workspace_size(pts, cam, o_u), dtype=torch.uint8, device=dev)
+    res["untiled_fwd_ms"] = round(timed(lambda: rast.rasterize_fwd_untiled(pts, cam, o_u, ws_u, out, stream)), 4)
+    rast.rasterize_profile_enable(True)
+    rast.rasterize_fwd_untiled(pts, cam, o_u, ws_u, out, stream)
+    prof = rast.rasterize_profile_read()
+    rast.rasterize_profile_enable(False)
+    res["untiled_kernels_ms"] = {k: round(b, 4) for k, (a, b) in prof.items()}
+    res["untiled_copies"] = int(rast.rasterize_get_status(ws_u, stream)[1]["n_copies"])
+    for tile in (16, 8):
+        o_t = rast.make_opts(mode="bilinear", tile=tile)
+        ws_t = torch.empty(rast.rasterize_workspace_size([_single(pts, cam, out)], o_t), dtype=torch.uint8,
+                           device=dev)
+        res[f"tiled{tile}_fwd_ms"] = round(timed(lambda: rast.rasterize_fwd(pts, cam, o_t, ws_t, out, stream)), 4)
+        if tile == 16:
+            res["tiled16_copies"] = int(rast.rasterize_get_status(ws_t, stream)[1]["n_copies"])
+    res["speedup_tiled16_vs_untiled"] = round(res["untiled_fwd_ms"] / res["tiled16_fwd_ms"], 3)
+    return res
+
+
+def _single(pts, cam, out):
+    from paper_2508_19140_gb300 import rast
+    v = rast.View()
+    v.pts, v.cam, v.out = pts, cam, out
+    return v
 
 
 def run_ring(scene, tens, opts, dev, stream, flush, reps, ms_single):

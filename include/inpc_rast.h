@@ -189,6 +189,20 @@ rast_status_t rasterize_batch(const rast_view_t* views, int32_t n_views, int32_t
                               const rast_opts_t* opts, void* workspace, size_t ws_bytes,
                               void* stream);
 
+/* Untiled baseline, forward only, bilinear only: the original INPC
+ * arrangement that Sec. 3.2 "Tiled Rendering" replaces. Every point makes one
+ * copy per pixel of its 2x2 footprint inside the image (about 4 per point
+ * instead of ~1.1 per 16x16 tile), the copies are sorted by (pixel, depth,
+ * point index) with the same split sort, and each pixel's list is composited
+ * by its own thread, gathering every fragment's record. Outputs are identical
+ * to rasterize_fwd (same per-pixel order and FP32 operations); it exists to
+ * measure what tiling saves on this GPU. opts->tile and blend_depth are
+ * ignored; RAST_ERR_NOT_SUPPORTED for Gaussian mode. */
+size_t rasterize_untiled_workspace_size(const rast_points_t* pts, const rast_camera_t* cam,
+                                        const rast_opts_t* opts);
+rast_status_t rasterize_fwd_untiled(const rast_points_t* pts, const rast_camera_t* cam, const rast_opts_t* opts,
+                                    void* workspace, size_t ws_bytes, const rast_images_t* out, void* stream);
+
 /* Several point clouds rendered into ONE image (the ring buffer of
  * view-specific clouds of Sec. 3.1 "Fast and Stable View-Specific Sampling
  * during Inference": the clouds sampled for the last frames are reused and

@@ -82,14 +82,17 @@ bool blend_depth_supported(int mode, int tile, int depth) {
 
 // cont[k] != 0: view k is another point cloud of view k - 1's image (same
 // camera, outputs and image gradients; its points join the same tile lists).
+// untiled: one "tile" per pixel (per-pixel lists, the untiled baseline).
 rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_opts_t* o, int pass,
-                        Plan& pl, const uint8_t* cont = nullptr) {
+                        Plan& pl, const uint8_t* cont = nullptr, bool untiled = false) {
     if (!views || !o || n_views < 1 || n_views > kMaxViews) return RAST_ERR_ARG;
     if (o->mode != RAST_SPLAT_BILINEAR && o->mode != RAST_SPLAT_GAUSSIAN) return RAST_ERR_ARG;
     if (o->gauss_cov != RAST_GAUSS_EWA && o->gauss_cov != RAST_GAUSS_ISO_SCREEN) return RAST_ERR_ARG;
-    if (o->tile != 8 && o->tile != 16) return RAST_ERR_NOT_SUPPORTED;
-    const int depth = o->blend_depth == 0 ? o->tile * o->tile : o->blend_depth;
-    if (!blend_depth_supported(o->mode, o->tile, depth)) return RAST_ERR_NOT_SUPPORTED;
+    const int T = untiled ? 1 : o->tile;
+    if (untiled && (o->mode != RAST_SPLAT_BILINEAR || (pass & RAST_PASS_BWD))) return RAST_ERR_NOT_SUPPORTED;
+    if (!untiled && o->tile != 8 && o->tile != 16) return RAST_ERR_NOT_SUPPORTED;
+    const int depth = untiled ? 1 : (o->blend_depth == 0 ? o->tile * o->tile : o->blend_depth);
+    if (!untiled && !blend_depth_supported(o->mode, o->tile, depth)) return RAST_ERR_NOT_SUPPORTED;
     if (!(o->t_min >= 0.f) || !(o->alpha_max > 0.f && o->alpha_max < 1.f)) return RAST_ERR_ARG;
     if (!(o->dilation >= 0.f) || o->max_copies < 0) return RAST_ERR_ARG;
     const int C = views[0].pts.channels;
@@ -104,7 +107,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     vt.bf16 = dt == RAST_BF16;
     vt.mode = o->mode;
     vt.gauss_cov = o->gauss_cov;
-    vt.tile = o->tile;
+    vt.tile = T;
     vt.blend_depth = depth;
     vt.t_min = o->t_min;
     vt.alpha_max = o->alpha_max;
@@ -122,7 +125,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
         if (v.pts.channels != C || v.pts.feat_dtype != dt) return RAST_ERR_ARG;
         const bool joins = cont && cont[k] && k > 0;
         if (!joins) prim = k;
-        rast_status_t st = check_view(v, pass, o->tile);
+        rast_status_t st = check_view(v, pass, T);
         if (st != RAST_OK) return st;
         ViewDev& d = vt.v[k];
         const rast_camera_t& c = v.cam;
@@ -133,8 +136,8 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
         d.far_z = c.far_z;
         d.W = c.width;
         d.H = c.height;
-        d.tiles_x = (c.width + o->tile - 1) / o->tile;
-        d.tiles_y = (c.height + o->tile - 1) / o->tile;
+        d.tiles_x = (c.width + T - 1) / T;
+        d.tiles_y = (c.height + T - 1) / T;
         d.key_base = f32_bits(c.near_z);
         d.key_cull = f32_bits(c.far_z) - f32_bits(c.near_z);
         if (d.key_cull > max_cull) max_cull = d.key_cull;
@@ -358,6 +361,7 @@ cudaError_t run_fwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
         RAST_TRY(radix_sort(k, v, 0, &b.hdr->n_copies, pl.copy_cap, pl.planC, sc, s, &rc, kTileSortNames));
     }
     RAST_TRY(launch_ranges(vt, b, b.keyC[rc], s));
+    if (vt.tile == 1) return launch_blend_fwd_pixel(vt, b, b.valC[rc], s);  // untiled baseline
     RAST_TRY(launch_tile_order(vt, b, s));
     RAST_TRY(launch_blend_fwd(vt, b, b.valC[rc], s));
     return cudaSuccess;
@@ -386,10 +390,11 @@ rast_view_t single_view(const rast_points_t* pts, const rast_camera_t* cam, cons
 
 // One launch sequence over the views (cont: see make_plan).
 rast_status_t run_views(const rast_view_t* views, int32_t n_views, int32_t pass, const rast_opts_t* opts,
-                        void* workspace, size_t ws_bytes, void* stream, const uint8_t* cont) {
+                        void* workspace, size_t ws_bytes, void* stream, const uint8_t* cont,
+                        bool untiled = false) {
     if (pass < 1 || pass > 3) return RAST_ERR_ARG;
     Plan pl;
-    const rast_status_t st = make_plan(views, n_views, opts, pass, pl, cont);
+    const rast_status_t st = make_plan(views, n_views, opts, pass, pl, cont, untiled);
     if (st != RAST_OK) return st;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return RAST_ERR_ARG;
     if (ws_bytes < pl.total) return RAST_ERR_CAPACITY;
@@ -521,6 +526,24 @@ rast_status_t rasterize_clouds(const rast_points_t* clouds, const rast_grads_t* 
 }  // extern "C"
 
 extern "C" {
+
+size_t rasterize_untiled_workspace_size(const rast_points_t* pts, const rast_camera_t* cam,
+                                        const rast_opts_t* opts) {
+    if (!pts || !cam) return 0;
+    rast_images_t dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    const rast_view_t v = single_view(pts, cam, &dummy, nullptr);
+    Plan pl;
+    if (make_plan(&v, 1, opts, 0, pl, nullptr, true) != RAST_OK) return 0;
+    return pl.total;
+}
+
+rast_status_t rasterize_fwd_untiled(const rast_points_t* pts, const rast_camera_t* cam, const rast_opts_t* opts,
+                                    void* workspace, size_t ws_bytes, const rast_images_t* out, void* stream) {
+    if (!pts || !cam || !out) return RAST_ERR_ARG;
+    const rast_view_t v = single_view(pts, cam, out, nullptr);
+    return run_views(&v, 1, RAST_PASS_FWD, opts, workspace, ws_bytes, stream, nullptr, true);
+}
 
 rast_status_t rasterize_fwd(const rast_points_t* pts, const rast_camera_t* cam, const rast_opts_t* opts,
                             void* workspace, size_t ws_bytes, const rast_images_t* out, void* stream) {

@@ -491,6 +491,98 @@ cudaError_t launch_tile_order(const ViewTable& vt, const Bufs& b, cudaStream_t s
     return cudaGetLastError();
 }
 
+namespace {
+
+// Untiled baseline (the per-pixel lists of the original INPC rasterizer that
+// Sec. 3.2 "Tiled Rendering" replaces): the copies are per-pixel fragments
+// sorted by (pixel, depth, point index), and one thread composites its
+// pixel's list front to back, gathering every fragment's record from memory.
+// Same FP32 operations as the tiled kernel, so the images are identical.
+template <int C, bool BF16>
+__global__ void __launch_bounds__(256) k_blend_fwd_pixel(const ViewTable vt, const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ pts,
+                                                         const uint32_t* __restrict__ rec,
+                                                         float* __restrict__ t_final, uint32_t* __restrict__ last_out,
+                                                         WsHeader* __restrict__ hdr) {
+    constexpr int RW = RecLayout<0, C, BF16>::words;
+    constexpr int FW = RecLayout<0, C, BF16>::feat_word;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // global pixel ("tile") id
+    const bool valid = p < vt.tiles_total;
+    uint32_t need = 0;
+    if (valid) {
+        const ViewDev& V = vt.v[view_of_tile(vt, p)];
+        const int64_t lp = p - V.tile_off;
+        const int px = (int)(lp % V.W), py = (int)(lp / V.W);
+        const uint2 rg = ranges[p];
+        const float amax = vt.alpha_max, tmin = vt.t_min;
+        float T = 1.f, A = 0.f, Dp = 0.f;
+        float F[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) F[c] = 0.f;
+        uint32_t last = 0, stop = 0;
+#pragma unroll 1
+        for (uint32_t q = rg.x; q < rg.y; ++q) {
+            const uint32_t* rp = rec + (size_t)pts[q] * RW;
+            const uint4 g = *reinterpret_cast<const uint4*>(rp);
+            const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
+            const float o = __uint_as_float(g.w);
+            const float wx = px == bg.i0 ? __fsub_rn(1.f, bg.a) : bg.a;
+            const float wy = py == bg.j0 ? __fsub_rn(1.f, bg.b) : bg.b;
+            const float alpha = fminf(__fmul_rn(o, __fmul_rn(wx, wy)), amax);
+            const float nT = __fmul_rn(T, __fsub_rn(1.f, alpha));
+            if (nT < tmin) {
+                stop = q - rg.x + 1;
+                break;
+            }
+            float f[C];
+            load_features<C, BF16>(rp + FW, f);
+            const float ta = T * alpha;
+#pragma unroll
+            for (int c = 0; c < C; ++c) F[c] = fmaf(ta, f[c], F[c]);
+            Dp = fmaf(ta, __uint_as_float(g.z), Dp);
+            A += ta;
+            T = nT;
+            last = q - rg.x + 1;
+        }
+        const int64_t pix = (int64_t)py * V.W + px;
+        float* of = V.out_feat + pix * C;
+#pragma unroll
+        for (int c = 0; c < C; ++c) of[c] = F[c];
+        if (V.out_alpha) V.out_alpha[pix] = A;
+        if (V.out_depth) V.out_depth[pix] = Dp;
+        t_final[V.pix_off + pix] = T;
+        last_out[V.pix_off + pix] = last;
+        need = stop ? stop : rg.y - rg.x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) need += __shfl_xor_sync(0xffffffffu, need, o);
+    if ((threadIdx.x & 31) == 0 && need) atomicAdd(&hdr->needed, (unsigned long long)need);
+}
+
+template <int C>
+cudaError_t launch_pixel_c(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    const unsigned grid = (unsigned)((vt.tiles_total + 255) / 256);
+    ProfScope ps("blend_fwd_pixel", s);
+    if (vt.bf16) k_blend_fwd_pixel<C, true><<<grid, 256, 0, s>>>(vt, b.ranges, pts, b.rec, b.t_final, b.last, b.hdr);
+    else k_blend_fwd_pixel<C, false><<<grid, 256, 0, s>>>(vt, b.ranges, pts, b.rec, b.t_final, b.last, b.hdr);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_blend_fwd_pixel(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    if (vt.tiles_total == 0) return cudaSuccess;
+    switch (vt.C) {
+        case 1: return launch_pixel_c<1>(vt, b, pts, s);
+        case 2: return launch_pixel_c<2>(vt, b, pts, s);
+        case 3: return launch_pixel_c<3>(vt, b, pts, s);
+        case 4: return launch_pixel_c<4>(vt, b, pts, s);
+        case 8: return launch_pixel_c<8>(vt, b, pts, s);
+        case 16: return launch_pixel_c<16>(vt, b, pts, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_blend_fwd(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     if (vt.tiles_total == 0) return cudaSuccess;
     switch (vt.C) {

@@ -221,6 +221,8 @@ cudaError_t launch_ranges(const ViewTable& vt, const Bufs& b, const uint32_t* so
 cudaError_t launch_tile_order(const ViewTable& vt, const Bufs& b, cudaStream_t s);
 cudaError_t launch_blend_fwd(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
                              cudaStream_t s);
+// Untiled baseline: one thread per pixel walks its per-pixel fragment list.
+cudaError_t launch_blend_fwd_pixel(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s);
 cudaError_t launch_point_scan(const ViewTable& vt, const Bufs& b, cudaStream_t s);
 cudaError_t launch_blend_bwd(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
                              cudaStream_t s);

@@ -109,6 +109,9 @@ SIGNATURES = {
                                                 ct.POINTER(WsEntry), ct.c_int32]),
     "rasterize_profile_enable": (None, [ct.c_int32]),
     "rasterize_profile_read": (ct.c_int32, [ct.POINTER(ProfileEntry), ct.c_int32]),
+    "rasterize_untiled_workspace_size": (ct.c_size_t, [ct.POINTER(Points), ct.POINTER(Camera), ct.POINTER(Opts)]),
+    "rasterize_fwd_untiled": (ct.c_int, [ct.POINTER(Points), ct.POINTER(Camera), ct.POINTER(Opts), ct.c_void_p,
+                                         ct.c_size_t, ct.POINTER(Images), ct.c_void_p]),
     "rasterize_clouds_workspace_size": (ct.c_size_t, [ct.POINTER(Points), ct.c_int32, ct.POINTER(Camera),
                                                       ct.POINTER(Opts)]),
     "rasterize_clouds": (ct.c_int, [ct.POINTER(Points), ct.POINTER(Grads), ct.c_int32, ct.POINTER(Camera),
@@ -312,6 +315,20 @@ def rasterize_profile_read() -> dict:
     n = L.rasterize_profile_read(ents, 64)
     return {ents[k].name.decode(): (int(ents[k].launches), float(ents[k].total_ms))
             for k in range(min(n, 64))}
+
+
+def rasterize_untiled_workspace_size(points: Points, camera: Camera, opts: Opts) -> int:
+    n = load_library().rasterize_untiled_workspace_size(ct.byref(points), ct.byref(camera), ct.byref(opts))
+    if n == 0:
+        raise RastError(RAST_ERR_ARG, "rasterize_untiled_workspace_size")
+    return int(n)
+
+
+def rasterize_fwd_untiled(points: Points, camera: Camera, opts: Opts, workspace, out: Images, stream=None):
+    _check(load_library().rasterize_fwd_untiled(ct.byref(points), ct.byref(camera), ct.byref(opts),
+                                                _ptr(workspace), int(workspace.numel() * workspace.element_size()),
+                                                ct.byref(out), _stream(stream)),
+           "rasterize_fwd_untiled")
 
 
 def rasterize_clouds_workspace_size(clouds, camera: Camera, opts: Opts) -> int:
