@@ -106,8 +106,8 @@ __global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs 
     uint32_t count = 0;
     uint32_t key = V.key_cull;
     if (vis) {
-        const int T = vt.tile;
-        const int tx0 = bx0 / T, tx1 = bx1 / T, ty0 = by0 / T, ty1 = by1 / T;
+        const int sh = __ffs(vt.tile) - 1;  // tile edges are powers of two (1, 8, 16)
+        const int tx0 = bx0 >> sh, tx1 = bx1 >> sh, ty0 = by0 >> sh, ty1 = by1 >> sh;
         rect = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
         count = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
         key = __float_as_uint(zc) - V.key_base;

@@ -75,11 +75,12 @@ struct WsHeader {
 
 // ---- small device helpers --------------------------------------------------
 
+// View of a global point index: views hold consecutive point ranges (pt_off
+// ascending); the loop runs n_views - 1 uniform iterations (none for one view).
 __device__ __forceinline__ int view_of_point(const ViewTable& vt, int64_t gi) {
     int v = 0;
-#pragma unroll
-    for (int k = 1; k < kMaxViews; ++k)
-        if (k < vt.n_views && gi >= vt.v[k].pt_off) v = k;
+    for (int k = 1; k < vt.n_views; ++k)
+        if (gi >= vt.v[k].pt_off) v = k;
     return v;
 }
 
