@@ -44,8 +44,50 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_warp
 }
 
 constexpr int kT = 256;
-constexpr int kPer = kScanItems / kT;  // 4 consecutive items per thread
-static_assert(kPer == 4, "the scans load four items per thread");
+constexpr int kPer = kScanItems / kT;  // consecutive items per thread
+static_assert(kPer % 4 == 0, "items move as 16-byte vectors");
+
+// kPer consecutive u32 / uint2 items starting at s0 (vector loads and stores
+// when the whole run is in range; `fill` past the end).
+__device__ __forceinline__ void load_u32s(const uint32_t* __restrict__ p, int64_t s0, int64_t n, uint32_t v[kPer],
+                                          uint32_t fill) {
+    if (s0 + kPer <= n) {
+#pragma unroll
+        for (int j = 0; j < kPer; j += 4) {
+            const uint4 q = *reinterpret_cast<const uint4*>(p + s0 + j);
+            v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) v[j] = s0 + j < n ? p[s0 + j] : fill;
+    }
+}
+
+__device__ __forceinline__ void load_rects(const uint2* __restrict__ p, int64_t s0, int64_t n, uint2 r[kPer]) {
+    if (s0 + kPer <= n) {
+#pragma unroll
+        for (int j = 0; j < kPer; j += 2) {
+            const uint4 q = *reinterpret_cast<const uint4*>(p + s0 + j);
+            r[j] = make_uint2(q.x, q.y);
+            r[j + 1] = make_uint2(q.z, q.w);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) r[j] = s0 + j < n ? p[s0 + j] : make_uint2(1u, 0u);
+    }
+}
+
+__device__ __forceinline__ void store_rects(uint2* __restrict__ p, int64_t s0, int64_t n, const uint2 r[kPer]) {
+    if (s0 + kPer <= n) {
+#pragma unroll
+        for (int j = 0; j < kPer; j += 2)
+            *reinterpret_cast<uint4*>(p + s0 + j) = make_uint4(r[j].x, r[j].y, r[j + 1].x, r[j + 1].y);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j)
+            if (s0 + j < n) p[s0 + j] = r[j];
+    }
+}
 
 // Sorted-order rects of a block of kScanItems points (gathered once, kept for
 // k_dup_write) and the block's copy count.
@@ -56,42 +98,17 @@ __global__ void __launch_bounds__(kT) k_dup_count(const uint32_t* __restrict__ s
     __shared__ uint32_t s_warp[33];
     const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
     uint32_t gi[kPer];
-    if (s0 + kPer <= n) {
-        const uint4 q = *reinterpret_cast<const uint4*>(sorted_pts + s0);
-        gi[0] = q.x; gi[1] = q.y; gi[2] = q.z; gi[3] = q.w;
-    } else {
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) gi[j] = s0 + j < n ? sorted_pts[s0 + j] : 0xffffffffu;
-    }
+    load_u32s(sorted_pts, s0, n, gi, 0xffffffffu);
     uint2 r[kPer];
 #pragma unroll
     for (int j = 0; j < kPer; ++j) r[j] = gi[j] != 0xffffffffu ? rect[gi[j]] : make_uint2(1u, 0u);
     uint32_t c = 0;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) c += rect_count(r[j]);
-    if (s0 + kPer <= n) {
-        uint4* d = reinterpret_cast<uint4*>(rectS + s0);
-        d[0] = make_uint4(r[0].x, r[0].y, r[1].x, r[1].y);
-        d[1] = make_uint4(r[2].x, r[2].y, r[3].x, r[3].y);
-    } else {
-#pragma unroll
-        for (int j = 0; j < kPer; ++j)
-            if (s0 + j < n) rectS[s0 + j] = r[j];
-    }
+    store_rects(rectS, s0, n, r);
     uint32_t tot;
     block_excl_scan<kT>(c, s_warp, tot);
     if (threadIdx.x == 0) blk[blockIdx.x] = tot;
-}
-
-// Four consecutive counts per thread (one 16-byte load when in range).
-__device__ __forceinline__ void load4(const uint32_t* __restrict__ p, int64_t s0, int64_t n, uint32_t v[4]) {
-    if (s0 + 4 <= n) {
-        const uint4 q = *reinterpret_cast<const uint4*>(p + s0);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = s0 + j < n ? p[s0 + j] : 0u;
-    }
 }
 
 __global__ void __launch_bounds__(kT) k_count_blocks(const uint32_t* __restrict__ cnt, int64_t n,
@@ -99,9 +116,12 @@ __global__ void __launch_bounds__(kT) k_count_blocks(const uint32_t* __restrict_
     __shared__ uint32_t s_warp[33];
     const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
     uint32_t v[kPer];
-    load4(cnt, s0, n, v);
+    load_u32s(cnt, s0, n, v, 0u);
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) sum += v[j];
     uint32_t tot;
-    block_excl_scan<kT>(v[0] + v[1] + v[2] + v[3], s_warp, tot);
+    block_excl_scan<kT>(sum, s_warp, tot);
     if (threadIdx.x == 0) blk[blockIdx.x] = tot;
 }
 
@@ -137,40 +157,51 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ blk
 }
 
 // Writes the copies: key = global tile id, value = global point index.
-__global__ void __launch_bounds__(kT) k_dup_write(const ViewTable vt, const uint32_t* __restrict__ sorted_pts,
-                                                  const uint2* __restrict__ rectS, int64_t n,
-                                                  const uint32_t* __restrict__ blk,
-                                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                  int64_t cap) {
+// Copies of a block of kScanItems depth-ordered points: 2 * kT threads with
+// half as many items each as the counting kernels (the per-item copy loops
+// are the long part here, so more threads beat more items per thread).
+constexpr int kTW = 2 * kT;
+constexpr int kPerW = kScanItems / kTW;
+
+__global__ void __launch_bounds__(kTW) k_dup_write(const ViewTable vt, const uint32_t* __restrict__ sorted_pts,
+                                                   const uint2* __restrict__ rectS, int64_t n,
+                                                   const uint32_t* __restrict__ blk,
+                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                   int64_t cap) {
     __shared__ uint32_t s_warp[33];
-    const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
-    uint2 r[kPer];
-    uint32_t gi[kPer];
-    if (s0 + kPer <= n) {
-        const uint4* q = reinterpret_cast<const uint4*>(rectS + s0);
-        const uint4 a = q[0], b = q[1];
-        r[0] = make_uint2(a.x, a.y); r[1] = make_uint2(a.z, a.w);
-        r[2] = make_uint2(b.x, b.y); r[3] = make_uint2(b.z, b.w);
-        const uint4 g = *reinterpret_cast<const uint4*>(sorted_pts + s0);
-        gi[0] = g.x; gi[1] = g.y; gi[2] = g.z; gi[3] = g.w;
+    const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPerW;
+    uint2 r[kPerW];
+    uint32_t gi[kPerW];
+    if (s0 + kPerW <= n) {
+#pragma unroll
+        for (int j = 0; j < kPerW; j += 2) {
+            const uint4 q = *reinterpret_cast<const uint4*>(rectS + s0 + j);
+            r[j] = make_uint2(q.x, q.y);
+            r[j + 1] = make_uint2(q.z, q.w);
+        }
+#pragma unroll
+        for (int j = 0; j < kPerW; j += 4) {
+            const uint4 q = *reinterpret_cast<const uint4*>(sorted_pts + s0 + j);
+            gi[j] = q.x; gi[j + 1] = q.y; gi[j + 2] = q.z; gi[j + 3] = q.w;
+        }
     } else {
 #pragma unroll
-        for (int j = 0; j < kPer; ++j) {
+        for (int j = 0; j < kPerW; ++j) {
             const bool ok = s0 + j < n;
             r[j] = ok ? rectS[s0 + j] : make_uint2(1u, 0u);
             gi[j] = ok ? sorted_pts[s0 + j] : 0u;
         }
     }
-    uint32_t c[kPer], sum = 0;
+    uint32_t c[kPerW], sum = 0;
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
+    for (int j = 0; j < kPerW; ++j) {
         c[j] = rect_count(r[j]);
         sum += c[j];
     }
     uint32_t tot;
-    uint32_t o = blk[blockIdx.x] + block_excl_scan<kT>(sum, s_warp, tot);
+    uint32_t o = blk[blockIdx.x] + block_excl_scan<kTW>(sum, s_warp, tot);
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
+    for (int j = 0; j < kPerW; ++j) {
         if (c[j] == 0) continue;
         const ViewDev& V = vt.v[view_of_point(vt, gi[j])];
         const int tx0 = r[j].x & 0xffff, ty0 = r[j].x >> 16, tx1 = r[j].y & 0xffff, ty1 = r[j].y >> 16;
@@ -193,9 +224,12 @@ __global__ void __launch_bounds__(kT) k_scan_apply(const uint32_t* __restrict__ 
     __shared__ uint32_t s_warp[33];
     const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
     uint32_t v[kPer];
-    load4(cnt, s0, n, v);
+    load_u32s(cnt, s0, n, v, 0u);
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) sum += v[j];
     uint32_t tot;
-    uint32_t o = blk[blockIdx.x] + block_excl_scan<kT>(v[0] + v[1] + v[2] + v[3], s_warp, tot);
+    uint32_t o = blk[blockIdx.x] + block_excl_scan<kT>(sum, s_warp, tot);
     uint32_t r[kPer];
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
@@ -203,7 +237,9 @@ __global__ void __launch_bounds__(kT) k_scan_apply(const uint32_t* __restrict__ 
         o += v[j];
     }
     if (s0 + kPer <= n) {
-        *reinterpret_cast<uint4*>(base + s0) = make_uint4(r[0], r[1], r[2], r[3]);
+#pragma unroll
+        for (int j = 0; j < kPer; j += 4)
+            *reinterpret_cast<uint4*>(base + s0 + j) = make_uint4(r[j], r[j + 1], r[j + 2], r[j + 3]);
     } else {
 #pragma unroll
         for (int j = 0; j < kPer; ++j)
@@ -267,7 +303,7 @@ cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t*
     }
     {
         ProfScope ps("dup.write", s);
-        k_dup_write<<<(unsigned)nb, kT, 0, s>>>(vt, sorted_pts, b.rectS, n, b.blk, b.keyC[0],
+        k_dup_write<<<(unsigned)nb, kTW, 0, s>>>(vt, sorted_pts, b.rectS, n, b.blk, b.keyC[0],
                                                b.valC[0], b.copy_cap);
     }
     return cudaGetLastError();

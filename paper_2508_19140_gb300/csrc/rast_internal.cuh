@@ -232,6 +232,6 @@ cudaError_t launch_reduce_grads(const ViewTable& vt, const Bufs& b, cudaStream_t
 bool channels_supported(int C);
 
 
-constexpr int kScanItems = 1024;   // items per block in the dup / point scans
+constexpr int kScanItems = 2048;   // items per block in the dup / point scans (8 per thread)
 
 }  // namespace rast
