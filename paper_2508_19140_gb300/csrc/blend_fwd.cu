@@ -1,34 +1,38 @@
-// K6: front-to-back blend per 16x16 tile (Eq. 1), one CTA per tile, one
-// thread per pixel.
+// K6: front-to-back blend per tile (Eq. 1), one CTA per tile (16x16 or 8x8
+// pixels), one thread per pixel.
 //
 // F = sum_i T_i a_i f_i, T_i = prod_{j<i} (1 - a_j), over the pixel's covering
 // fragments in (depth, point index) order, stopping before the first fragment
 // that would take T below t_min. Each CTA walks its tile's sorted list in
-// batches of 256 records: every thread gathers one record (two or three
-// 128-bit loads of a 16-byte aligned record) and stages it in shared memory,
-// then each pixel composites the records of the batch that cover it, in list
-// order. The loads of batch b+1 (and the point indices of batch b+2) are issued
-// before batch b is composited, so the gather latency overlaps the compositing
+// batches of D records (the blend depth: tile^2 x RPT): every thread gathers
+// its RPT records with 16-byte cp.async copies into a shared-memory ring (two
+// or three batches deep, padded stride against bank conflicts), and each pixel
+// composites the records of the batch that cover it, in list order. The copies
+// of the next batches (and the point indices of the ones after) are in flight
+// while a batch is composited, so the gather latency overlaps the compositing
 // instead of adding to every batch of the tile's serial chain.
 //
 // Bilinear splats touch at most 4 pixels, so testing every record against
-// every pixel (256 tests per record) would make the kernel ALU-bound. Instead
-// the record's thread sets one bit per covered pixel in a per-pixel 256-bit
-// mask (shared-memory atomicOr, order-free and therefore deterministic), and
-// each pixel visits only its set bits in ascending order = list order.
+// every pixel would make the kernel ALU-bound. Instead the record's thread
+// computes its four slot alphas once (the oracle's FP32 operations) and sets
+// one bit per covered pixel in a per-pixel D-bit mask (shared-memory atomicOr,
+// order-free and therefore deterministic); each pixel visits only its set bits
+// in ascending order = list order.
 //
 // Gaussian splats cover many pixels; there each warp owns an 8x4 sub-tile,
 // ballots the batch's records whose pixel box overlaps the sub-tile, and
 // composites only those, all 32 lanes in lockstep.
 //
-// Tiles are visited heaviest first (k_tile_order): the blend's duration is
-// bounded below by its longest tile list, so that list must start at once.
-// The CTA stops reading as soon as every in-image pixel has terminated
-// (__syncthreads_count), which is where early termination saves HBM traffic.
-// Saved for the backward pass: T_final and the 1-based list position of the
-// last blended fragment per pixel. The per-tile count of records the method had
-// to read (every record if some pixel never terminated, else up to the last
-// terminating fragment) is summed into the workspace header.
+// Tiles are visited heaviest first (k_tile_buckets / k_tile_scatter): the
+// blend's duration is bounded below by its longest tile list, so that list
+// must start at once. The CTA stops reading as soon as every in-image pixel
+// has terminated (__syncthreads_count), which is where early termination saves
+// HBM traffic. Saved for the backward pass: T_final and the 1-based list
+// position of the last blended fragment per pixel. The per-tile count of
+// records the method had to read (every record if some pixel never terminated,
+// else up to the last terminating fragment) is summed into the workspace
+// header. The untiled baseline's per-pixel kernel (k_blend_fwd_pixel) is at
+// the end of the file.
 #include "blend_common.cuh"
 
 namespace rast {

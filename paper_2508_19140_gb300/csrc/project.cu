@@ -10,8 +10,9 @@
 //   x_c = ((R0 x + R1 y) + R2 z) + t0,  u = fx (x_c / z_c) + cx,
 //   bilinear box {floor(u - 1/2), +1} x {floor(v - 1/2), +1},
 //   Gaussian box [ceil(u - 1/2 - r), floor(u - 1/2 + r)], r = ceil(3 sqrt(lambda_max)).
-// Output per point: a record (u, v, z, o[, conic a b c, r], features) padded to
-// 16-byte multiples so the blend gathers it with 128-bit loads, the depth key
+// Output per point: a record (u, v, z, o[, conic a b c, r], features) with a
+// power-of-two stride of 32-128 bytes (one DRAM burst per gather, 16-byte
+// chunks for the blends' cp.async copies), the depth key
 // bits(z) - bits(near) for the split sort's first stage, the tile rect and the
 // number of tiles it touches.
 #include "rast_internal.cuh"
