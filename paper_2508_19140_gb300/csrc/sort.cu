@@ -410,7 +410,10 @@ SortPlan make_sort_plan(int bits) {
         p.passes = 0;
         return p;
     }
-    int passes = (bits + 8) / 9;
+    // Up to 9-bit digits for short keys (tile ids); 7-bit digits for long keys
+    // (depth): measured, four 7-bit passes over 27-bit depth keys beat three
+    // 9-bit ones (fewer ballots and bins per pass, more CTAs per SM).
+    int passes = bits > 18 ? (bits + 6) / 7 : (bits + 8) / 9;
     int per = (bits + passes - 1) / passes;
     if (per < 4) per = 4;
     int shift = 0;
