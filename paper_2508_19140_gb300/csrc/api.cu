@@ -204,8 +204,8 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     pl.bytes[S_KEYC0] = pl.bytes[S_KEYC1] = pl.bytes[S_VALC0] = pl.bytes[S_VALC1] = (size_t)D * 4;
     pl.bytes[S_PARTIAL] = (size_t)D * pl.partial_floats * 4;
     pl.bytes[S_GROW] = o->mode == RAST_SPLAT_BILINEAR ? (size_t)N * grow_stride(C + 1) * 4 : 0;
-    pl.bytes[S_SGHIST] = (size_t)4 * 512 * 4;
-    pl.bytes[S_SCOUNT] = (size_t)4 * 4;
+    pl.bytes[S_SGHIST] = (size_t)kMaxSortPasses * 512 * 4;
+    pl.bytes[S_SCOUNT] = (size_t)kMaxSortPasses * 4;
     {
         const int64_t wa = sort_status_words(pl.planA, npt), wc = sort_status_words(pl.planC, pl.copy_cap);
         pl.bytes[S_SSTATUS] = (size_t)(wa > wc ? wa : wc) * 4;

@@ -172,7 +172,7 @@ struct Bufs {
     float* grow;          // backward gradient rows of single-copy points, indexed by point
     // radix sort scratch
     uint32_t* sort_ghist;     // [passes][bins] digit counts
-    uint32_t* sort_counters;  // [4] tile counters of the passes
+    uint32_t* sort_counters;  // [kMaxSortPasses] tile counters of the passes
     uint32_t* sort_status;    // [passes][tiles][bins] look-back words
     // per tile / pixel
     uint2* ranges;
@@ -187,6 +187,10 @@ struct Bufs {
 };
 
 // Sort plan for one radix sort: digit passes over [0, bits).
+// Most digit passes one radix sort runs: the digit counts, the per-pass tile
+// counters and the histogram kernel's shared counts are sized for this many.
+constexpr int kMaxSortPasses = 4;
+
 struct SortPlan {
     int passes;
     int digit_bits[8];
@@ -197,8 +201,8 @@ SortPlan make_sort_plan(int bits);
 int64_t sort_status_words(const SortPlan& plan, int64_t cap);
 
 struct SortScratch {
-    uint32_t* ghist;     // [4][512]
-    uint32_t* counters;  // [4]
+    uint32_t* ghist;     // [kMaxSortPasses][512]
+    uint32_t* counters;  // [kMaxSortPasses]
     uint32_t* status;    // sort_status_words()
     uint32_t* err;       // workspace error word
 };

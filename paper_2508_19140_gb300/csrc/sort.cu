@@ -98,11 +98,11 @@ __global__ void __launch_bounds__(kThreads) k_digit_hist(const uint32_t* __restr
                                                          uint32_t* __restrict__ counters,
                                                          uint32_t* __restrict__ status, int64_t tiles_cap) {
     constexpr int BINS = 1 << BITS;
-    __shared__ uint32_t s_h[4 * BINS];
+    __shared__ uint32_t s_h[kMaxSortPasses * BINS];
     const int64_t n = read_count(n_host, d_n);
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
     for (int i = threadIdx.x; i < passes * BINS; i += kThreads) s_h[i] = 0;
-    if (blockIdx.x == 0 && threadIdx.x < 4) counters[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < kMaxSortPasses) counters[threadIdx.x] = 0;
     for (int p = 0; p < passes; ++p) {
         uint32_t* st = status + (int64_t)p * tiles_cap * BINS;
         const int64_t words = ntiles * BINS;
@@ -413,7 +413,10 @@ SortPlan make_sort_plan(int bits) {
     // Up to 9-bit digits for short keys (tile ids); 7-bit digits for long keys
     // (depth): measured, four 7-bit passes over 27-bit depth keys beat three
     // 9-bit ones (fewer ballots and bins per pass, more CTAs per SM).
+    // Keys wider than 28 bits (a far/near ratio beyond about 2^29) take four
+    // wider digits: the scratch buffers hold at most kMaxSortPasses passes.
     int passes = bits > 18 ? (bits + 6) / 7 : (bits + 8) / 9;
+    if (passes > kMaxSortPasses) passes = kMaxSortPasses;
     int per = (bits + passes - 1) / passes;
     if (per < 4) per = 4;
     int shift = 0;
@@ -436,6 +439,7 @@ cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const ui
                        const char* const names[2], bool identity_vals) {
     *result_buf = 0;
     if (plan.passes == 0 || cap == 0) return cudaSuccess;
+    if (plan.passes > kMaxSortPasses) return cudaErrorInvalidValue;
     switch (plan.digit_bits[0]) {
         case 4: return sort_t<4>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
         case 5: return sort_t<5>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);

@@ -358,3 +358,32 @@ def test_capacity_overflow_is_reported_not_written():
     assert st == 2  # RAST_ERR_CAPACITY
     F, A, _ = r.image()  # nothing is blended from a truncated list
     assert np.all(F == 0) and np.all(A == 0)
+
+
+def test_wide_depth_range_uses_widest_digits():
+    """near 1e-4, far 1e8: depth keys bits(z) - bits(near) of 29 bits, which the
+    split sort covers with its widest digits (four 8-bit passes)."""
+    cam = scenes.identity_camera(96, 64, 80.0)
+    cam.near, cam.far = 1e-4, 1e8
+    rng = np.random.default_rng(27)
+    n = 6000
+    u = rng.uniform(-2.0, cam.width + 2.0, n)
+    w = rng.uniform(-2.0, cam.height + 2.0, n)
+    z = np.exp(rng.uniform(np.log(2e-4), np.log(5e7), n))
+    z[:20] = 2e8  # beyond far
+    z[20:25] = 5e-5  # inside near
+    xyz = np.stack([(u - cam.cx) * z / cam.fx, (w - cam.cy) * z / cam.fy, z], 1)
+    v = _view(xyz, rng.uniform(0.05, 0.9, n), rng.random((n, 4)), cam, seed=27)
+    r = Run([v], backward=True)
+    assert r.status == 0
+    tiles, idx = oracle.tile_lists(v.xyz, cam, **oracle_kw("bilinear"))
+    keys, vals = r.sorted_copies()
+    assert np.array_equal(keys, tiles) and np.array_equal(vals, idx)
+    ref = oracle.render(v.xyz, v.opacity, v.feat, cam, **oracle_kw("bilinear"))
+    _check_image(r, ref)
+    _, last = r.pixel_state()
+    assert np.array_equal(last, ref["last_pos"].astype(np.uint32))
+    g = oracle.backward(v.xyz, v.opacity, v.feat, cam, v.g_feat, v.g_alpha, v.g_depth,
+                        **oracle_kw("bilinear"))
+    _check_grad(r.grads()["d_feat"], g["d_feat"])
+    _check_grad(r.grads()["d_opacity"], g["d_opacity"])
