@@ -125,6 +125,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
         if (v.pts.channels != C || v.pts.feat_dtype != dt) return RAST_ERR_ARG;
         const bool joins = cont && cont[k] && k > 0;
         if (!joins) prim = k;
+        if (joins) vt.shared_tiles = 1;
         rast_status_t st = check_view(v, pass, T);
         if (st != RAST_OK) return st;
         ViewDev& d = vt.v[k];

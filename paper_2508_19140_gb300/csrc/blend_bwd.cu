@@ -19,8 +19,10 @@
 // filled by a fixed-order shuffle reduction), and written to the copy's own
 // slot base[i] + (rank of the tile in the point's tile rect); a bilinear point
 // with a single copy writes its row to a per-point array instead (whole
-// sectors, no slot base needed). K8 then sums a point's slots in rect order and
-// writes the outputs with coalesced stores. A per-tile cutoff (depth bits and
+// sectors, no slot base needed), or, when its FP32 dL/df row is itself whole
+// sectors (C a multiple of 8), writes dL/df to the output and keeps only dL/do
+// in the per-point array (one whole sector per point). K8 then sums a point's
+// slots in rect order and writes the outputs with coalesced stores. A per-tile cutoff (depth bits and
 // point index of the last record the replay touched) tells K8 which slots were
 // written.
 #include "blend_common.cuh"
@@ -40,6 +42,15 @@ __device__ __forceinline__ uint32_t block_max_u32(uint32_t x, uint32_t* s) {
 
 // ---------------------------------------------------------------- bilinear
 
+// On 16x16 tiles a bilinear point with one copy and C a multiple of 8 (its
+// FP32 dL/df row is then whole 32-byte sectors) has dL/df written straight to
+// the output by the blend and only dL/do kept for K8, alone in a 32-byte
+// sector of its own (a 4-byte scattered store leaves a partial sector, which
+// HBM must read-modify-write). 8x8 tiles keep the whole per-point row
+// (measured faster there). Either layout fits the grow_stride(C + 1) rows.
+__host__ __device__ constexpr bool direct_feat_grads(int C, int tile) { return C % 8 == 0 && tile == 16; }
+constexpr int kOpRow = 8;  // floats per point of the dL/do sectors
+
 // cp.async ring depth (batches in flight per CTA): three batches for 16x16
 // tiles with one record per thread; two otherwise (deeper batches hide more
 // latency each, and 8x8 tiles gain more from the extra CTAs per SM that a
@@ -57,8 +68,10 @@ constexpr size_t bilinear_bwd_smem() {
 }
 
 // RPT = records each thread stages per batch (blend depth D = TS * TS * RPT).
+// 8x8 tiles with one record per thread: held to 64 registers, so the 16 CTAs
+// per SM that shared memory allows stay resident (no spills at that bound).
 template <int TS, int RPT, int C, bool BF16>
-__global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
+__global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend_bwd_bilinear(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec,
     const float* __restrict__ t_final, const uint32_t* __restrict__ last_in,
@@ -314,12 +327,23 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_bilinear(
                 acc[C] += s_da[sl * D + r];
             }
             if (single[k]) {
-                // Sole copy: the point's gradient, in a whole-sector row of its own
-                // (K8 copies it to the outputs with coalesced writes).
-                float row[GS];
+                if constexpr (direct_feat_grads(C, TS)) {
+                    // Sole copy, dL/df rows of whole sectors: final, straight to
+                    // the output; dL/do waits for K8 in a whole sector of its own.
+                    const ViewDev& Vp = vt.shared_tiles ? vt.v[view_of_point(vt, gi_rec[k])] : V;
+                    if (Vp.d_feat) store_row<C>(Vp.d_feat + ((int64_t)gi_rec[k] - Vp.pt_off) * C, acc);
+                    float row[kOpRow];
 #pragma unroll
-                for (int q = 0; q < GS; ++q) row[q] = q < P ? acc[q] : 0.f;
-                store_row<GS>(grow + (size_t)gi_rec[k] * GS, row);
+                    for (int q = 0; q < kOpRow; ++q) row[q] = q == 0 ? acc[C] : 0.f;
+                    store_row<kOpRow>(grow + (size_t)gi_rec[k] * kOpRow, row);
+                } else {
+                    // Sole copy: the point's gradient, in a whole-sector row of its
+                    // own (K8 copies it to the outputs with coalesced writes).
+                    float row[GS];
+#pragma unroll
+                    for (int q = 0; q < GS; ++q) row[q] = q < P ? acc[q] : 0.f;
+                    store_row<GS>(grow + (size_t)gi_rec[k] * GS, row);
+                }
             } else {
                 float row[PS];
 #pragma unroll
@@ -570,7 +594,65 @@ __global__ void __launch_bounds__(256, 6) k_reduce_grads(const ViewTable vt, con
     const uint32_t zb = zbits[gi];
     const uint32_t pbase = base[gi];
     const uint32_t cnt = rect_count(rc);
-    if (cnt) {
+    if constexpr (MODE == 0 && direct_feat_grads(C, 16)) {
+        if (cnt == 1 && vt.tile == 16) {
+            // One copy: the blend wrote dL/df itself if its replay reached the
+            // point; dL/do waits in the per-point array.
+            const uint2 co = cutoff[V.tile_off + (int64_t)(rc.x >> 16) * V.tiles_x + (rc.x & 0xffff)];
+            const bool done = zb < co.x || (zb == co.x && (uint32_t)gi <= co.y);
+            if (V.d_opacity) V.d_opacity[i] = done ? grow[(size_t)gi * kOpRow] : 0.f;
+            if (!done && V.d_feat) store_row<C>(V.d_feat + i * C, acc);
+            if (V.d_xyz) {
+                V.d_xyz[3 * i] = 0.f;
+                V.d_xyz[3 * i + 1] = 0.f;
+                V.d_xyz[3 * i + 2] = 0.f;
+            }
+            if (V.d_scale) V.d_scale[i] = 0.f;
+            return;
+        }
+    }
+    if (MODE == 0 && cnt) {
+        // Bilinear: one, two or four tiles. The cutoffs of all of them first,
+        // then the rows (two at a time for C <= 11), so a point waits on two
+        // memory round trips rather than two per tile; rows still add up in
+        // rect order.
+        const int tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff;
+        const int w = tx1 - tx0 + 1;
+        bool dn[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            dn[k] = false;
+            if (k < (int)cnt) {
+                const uint2 co = cutoff[V.tile_off + (int64_t)(ty0 + k / w) * V.tiles_x + (tx0 + k % w)];
+                dn[k] = zb < co.x || (zb == co.x && (uint32_t)gi <= co.y);
+            }
+        }
+        // A point with one copy has its row indexed by point.
+        const float* pp = cnt == 1 ? grow + (size_t)gi * GS : partial + (size_t)pbase * PS;
+        constexpr int KB = PS <= 12 ? 2 : 1;  // rows in flight (wide rows one at a time: no spills)
+#pragma unroll
+        for (int k0 = 0; k0 < 4; k0 += KB) {
+            if (k0 >= (int)cnt) break;
+            float4 x[KB][PS / 4];
+#pragma unroll
+            for (int h = 0; h < KB; ++h)
+#pragma unroll
+                for (int j = 0; j < PS / 4; ++j)
+                    x[h][j] = dn[k0 + h] ? reinterpret_cast<const float4*>(pp + (size_t)(k0 + h) * PS)[j]
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int h = 0; h < KB; ++h) {
+                if (!dn[k0 + h]) continue;
+#pragma unroll
+                for (int j = 0; j < PS / 4; ++j) {
+                    if (4 * j + 0 < P) acc[4 * j + 0] += x[h][j].x;
+                    if (4 * j + 1 < P) acc[4 * j + 1] += x[h][j].y;
+                    if (4 * j + 2 < P) acc[4 * j + 2] += x[h][j].z;
+                    if (4 * j + 3 < P) acc[4 * j + 3] += x[h][j].w;
+                }
+            }
+        }
+    } else if (cnt) {
         const int tx0 = rc.x & 0xffff, ty0 = rc.x >> 16, tx1 = rc.y & 0xffff, ty1 = rc.y >> 16;
         const float* pp = partial + (size_t)pbase * PS;
         int k = 0;

@@ -56,6 +56,7 @@ struct ViewTable {
     int32_t blend_depth; // records per blend batch: tile^2 x {1, 2} (x 4 for tile 8); Gaussian: tile^2
     int32_t rec_words;   // record stride in 32-bit words (multiple of 4)
     int32_t feat_word;   // first feature word in a record
+    int32_t shared_tiles; // some view blends into another view's tiles (point clouds of one image)
     float t_min, alpha_max, dilation;
     int64_t n_total, tiles_total, pix_total;
     ViewDev v[kMaxViews];
