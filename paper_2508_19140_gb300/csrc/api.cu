@@ -350,8 +350,9 @@ cudaError_t run_fwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
         uint32_t* k[2] = {b.keyA[0], b.keyA[1]};
         uint32_t* v[2] = {b.valA[0], b.valA[1]};
         const SortScratch sc{b.sort_ghist, b.sort_counters, b.sort_status, &b.hdr->error};
+        // Only the depth order of the point indices is used after this sort.
         RAST_TRY(radix_sort(k, v, vt.n_total, nullptr, vt.n_total, pl.planA, sc, s, &ra, kDepthSortNames,
-                            true));
+                            true, false));
     }
     const uint32_t* depth_sorted = b.valA[ra];
     RAST_TRY(launch_duplicate(vt, b, depth_sorted, s));

@@ -216,10 +216,11 @@ cudaError_t launch_project(const ViewTable& vt, const Bufs& b, bool write_vals, 
 // *result_buf to the index (0/1) of the buffer that holds the result.
 // names: profiling names of the digit-count kernel and of the sweep passes.
 // identity_vals: the input values are their own positions (0, 1, 2, ...);
-// vals[0] is then not read.
+// vals[0] is then not read. keys_out = false: only the values are wanted, the
+// last pass does not write keys (keys[*result_buf] is left stale).
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n, int64_t cap,
                        const SortPlan& plan, const SortScratch& sc, cudaStream_t s, int* result_buf,
-                       const char* const names[2], bool identity_vals = false);
+                       const char* const names[2], bool identity_vals = false, bool keys_out = true);
 cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
                              cudaStream_t s);
 cudaError_t launch_ranges(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_tiles,

@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
             const uint32_t key = s_keys[j];
             const uint32_t d = (key >> shift) & (BINS - 1);
             const uint32_t dst = s_gbase[d] + ((uint32_t)j - s_excl[d]);
-            kout[dst] = key;
+            if (kout) kout[dst] = key;
             vout[dst] = s_vals[j];
         }
         __syncthreads();
@@ -350,7 +350,7 @@ size_t sweep_smem() {
 template <int BITS>
 cudaError_t sort_t(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n, int64_t cap,
                    const SortPlan& plan, const SortScratch& sc, cudaStream_t s, int* result_buf,
-                   const char* const names[2], bool identity_vals) {
+                   const char* const names[2], bool identity_vals, bool keys_out) {
     constexpr int BINS = 1 << BITS;
     static bool attr_set = false;
     const size_t smem = sweep_smem<BITS>();
@@ -391,7 +391,8 @@ cudaError_t sort_t(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32
     for (int k = 0; k < plan.passes; ++k) {
         ProfScope ps(names[1], s);
         auto kern = (k == 0 && identity_vals) ? k_sweep<BITS, true> : k_sweep<BITS, false>;
-        kern<<<gs, kThreads, smem, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, d_n,
+        uint32_t* kout = (k + 1 == plan.passes && !keys_out) ? nullptr : keys[cur ^ 1];
+        kern<<<gs, kThreads, smem, s>>>(keys[cur], vals[cur], kout, vals[cur ^ 1], n, d_n,
                                                  plan.shift[k], sc.ghist + k * BINS, sc.counters + k,
                                                  sc.status + (int64_t)k * tiles_cap * BINS, sc.err);
         e = cudaGetLastError();
@@ -436,17 +437,17 @@ int64_t sort_status_words(const SortPlan& plan, int64_t cap) {
 
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32_t* d_n, int64_t cap,
                        const SortPlan& plan, const SortScratch& sc, cudaStream_t s, int* result_buf,
-                       const char* const names[2], bool identity_vals) {
+                       const char* const names[2], bool identity_vals, bool keys_out) {
     *result_buf = 0;
     if (plan.passes == 0 || cap == 0) return cudaSuccess;
     if (plan.passes > kMaxSortPasses) return cudaErrorInvalidValue;
     switch (plan.digit_bits[0]) {
-        case 4: return sort_t<4>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
-        case 5: return sort_t<5>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
-        case 6: return sort_t<6>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
-        case 7: return sort_t<7>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
-        case 8: return sort_t<8>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
-        case 9: return sort_t<9>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals);
+        case 4: return sort_t<4>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals, keys_out);
+        case 5: return sort_t<5>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals, keys_out);
+        case 6: return sort_t<6>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals, keys_out);
+        case 7: return sort_t<7>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals, keys_out);
+        case 8: return sort_t<8>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals, keys_out);
+        case 9: return sort_t<9>(keys, vals, n, d_n, cap, plan, sc, s, result_buf, names, identity_vals, keys_out);
         default: return cudaErrorInvalidValue;
     }
 }

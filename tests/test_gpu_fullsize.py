@@ -34,13 +34,14 @@ def frame():
 def test_depth_sort_is_sorted_permutation(frame):
     v, r = frame
     n = len(v.xyz)
-    keys = r.arr("keys_a0", np.uint32, n) if r.layout["depth_sorted"][0] == r.layout["vals_a0"][0] \
-        else r.arr("keys_a1", np.uint32, n)
     vals = r.arr("depth_sorted", np.uint32, n)
-    assert np.all(np.diff(keys.astype(np.int64)) >= 0)
     assert np.array_equal(np.sort(vals), np.arange(n, dtype=np.uint32))
     p = oracle.project(v.xyz, v.camera, **KW)
     zb = p["zbits"].astype(np.int64)
+    # depth keys in sorted order: bits(z) - bits(near), culled points last
+    f32 = lambda x: int(np.float32(x).view(np.uint32))
+    key = np.where(p["vis"] == 1, zb - f32(v.camera.near), f32(v.camera.far) - f32(v.camera.near))
+    assert np.all(np.diff(key[vals]) >= 0)
     vis = p["vis"][vals] == 1
     z = zb[vals][vis]
     iv = vals[vis].astype(np.int64)
