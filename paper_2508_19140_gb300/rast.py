@@ -476,11 +476,16 @@ class _Batch(torch.autograd.Function):
             v.cam = make_camera(ctx.cams[k])
             v.grad = make_grads(gF, gA, gD, d_feat, d_op, d_xyz, d_scale)
             views.append(v)
-            grads_out += [d_xyz, d_op, d_feat.to(ctx.feat_dtypes[k]), d_scale]
+            grads_out.append([d_xyz, d_op, d_feat, d_scale])
             # keep upstream gradient tensors alive until the launch is enqueued
             v._keep = (gF, gA, gD)
         rasterize_batch(views, PASS_BWD, opts, ws)
-        return (None, None, None, None) + tuple(grads_out)
+        flat = []
+        for k, (d_xyz, d_op, d_feat, d_scale) in enumerate(grads_out):
+            # dL/df is FP32; cast to the features' dtype only after the kernels
+            # that write it are enqueued
+            flat += [d_xyz, d_op, d_feat.to(ctx.feat_dtypes[k]), d_scale]
+        return (None, None, None, None) + tuple(flat)
 
 
 def rasterize_views(items, mode="bilinear", gauss_cov="ewa", check=True, **opt_kw):
