@@ -229,10 +229,13 @@ rast_status_t rasterize_get_status(const void* workspace, size_t ws_bytes, void*
 /* Human-readable name of a status code (static storage). */
 const char* rasterize_status_string(rast_status_t status);
 
-/* Byte offsets of the workspace arrays, for inspection by tests:
- * names "records", "rect", "count", "sorted_vals", "sorted_keys", "ranges",
- * "t_final", "last", "header"; writes up to `max` (name, offset, bytes)
- * triples and returns how many exist. Layout only: no device access. */
+/* Byte offsets of the workspace arrays, for inspection by tests: one entry
+ * per internal array ("header", "records", "rect", "count", "ranges",
+ * "t_final", "last", ...) plus three aliases of the sort results:
+ * "depth_sorted" (point indices in depth order), "sorted_keys" and
+ * "sorted_vals" (tile id and point index of every copy, in (tile, depth bits,
+ * point index) order). Writes up to `max` (name, offset, bytes) triples and
+ * returns how many exist. Layout only: no device access. */
 typedef struct { char name[24]; int64_t offset; int64_t bytes; } rast_ws_entry_t;
 int32_t rasterize_workspace_layout(const rast_view_t* views, int32_t n_views,
                                    const rast_opts_t* opts, rast_ws_entry_t* out, int32_t max);

@@ -196,6 +196,11 @@ def make_camera(cam) -> Camera:
     return c
 
 
+def _nbytes(t) -> int:
+    """Size in bytes of a workspace or scratch tensor (any dtype)."""
+    return int(t.numel() * t.element_size())
+
+
 def _ptr(t):
     if t is None:
         return None
@@ -260,7 +265,7 @@ def rasterize_workspace_size(views, opts: Opts) -> int:
 
 def rasterize_fwd(points: Points, camera: Camera, opts: Opts, workspace, out: Images, stream=None):
     s = load_library().rasterize_fwd(ct.byref(points), ct.byref(camera), ct.byref(opts),
-                                     _ptr(workspace), workspace.numel(), ct.byref(out), _stream(stream))
+                                     _ptr(workspace), _nbytes(workspace), ct.byref(out), _stream(stream))
     _check(s, "rasterize_fwd")
 
 
@@ -275,20 +280,20 @@ def rasterize_fwd_noalloc(points: Points, camera: Camera, opts: Opts, out: Image
 
 def rasterize_bwd(points: Points, camera: Camera, opts: Opts, workspace, grads: Grads, stream=None):
     s = load_library().rasterize_bwd(ct.byref(points), ct.byref(camera), ct.byref(opts),
-                                     _ptr(workspace), workspace.numel(), ct.byref(grads), _stream(stream))
+                                     _ptr(workspace), _nbytes(workspace), ct.byref(grads), _stream(stream))
     _check(s, "rasterize_bwd")
 
 
 def rasterize_batch(views, pass_: int, opts: Opts, workspace, stream=None):
     arr = _view_array(views)
     s = load_library().rasterize_batch(arr, len(views), int(pass_), ct.byref(opts), _ptr(workspace),
-                                       workspace.numel(), _stream(stream))
+                                       _nbytes(workspace), _stream(stream))
     _check(s, "rasterize_batch")
 
 
 def rasterize_get_status(workspace, stream=None):
     st = Stats()
-    s = load_library().rasterize_get_status(_ptr(workspace), workspace.numel(), _stream(stream),
+    s = load_library().rasterize_get_status(_ptr(workspace), _nbytes(workspace), _stream(stream),
                                             ct.byref(st))
     stats = {f: getattr(st, f) for f, _ in Stats._fields_}
     return int(s), stats
@@ -326,7 +331,7 @@ def rasterize_untiled_workspace_size(points: Points, camera: Camera, opts: Opts)
 
 def rasterize_fwd_untiled(points: Points, camera: Camera, opts: Opts, workspace, out: Images, stream=None):
     _check(load_library().rasterize_fwd_untiled(ct.byref(points), ct.byref(camera), ct.byref(opts),
-                                                _ptr(workspace), int(workspace.numel() * workspace.element_size()),
+                                                _ptr(workspace), _nbytes(workspace),
                                                 ct.byref(out), _stream(stream)),
            "rasterize_fwd_untiled")
 
@@ -346,7 +351,7 @@ def rasterize_clouds(clouds, grads, camera: Camera, out: Images, pass_: int, opt
     garr = None if grads is None else (Grads * len(grads))(*grads)
     _check(load_library().rasterize_clouds(arr, garr, len(clouds), ct.byref(camera), ct.byref(out), int(pass_),
                                            ct.byref(opts), _ptr(workspace),
-                                           int(workspace.numel() * workspace.element_size()), _stream(stream)),
+                                           _nbytes(workspace), _stream(stream)),
            "rasterize_clouds")
 
 
@@ -383,7 +388,7 @@ def rasterize_bg_composite_bwd(camera: Camera, env: EnvMap, dirs, alpha, g, g_al
                                stream=None):
     _check(load_library().rasterize_bg_composite_bwd(ct.byref(camera), ct.byref(env), _ptr(dirs), _ptr(alpha),
                                                      _ptr(g), _ptr(g_alpha), _ptr(d_map), _ptr(scratch),
-                                                     int(scratch.numel() * scratch.element_size()),
+                                                     _nbytes(scratch),
                                                      _stream(stream)),
            "rasterize_bg_composite_bwd")
 
