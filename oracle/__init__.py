@@ -18,7 +18,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
 _SRCS = [_SRC, os.path.join(_HERE, "envmap.cpp")]
 _OUT_DIR = os.path.join(_HERE, "_build")
-_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+# A prebuilt oracle library to load instead of building this one: the
+# planted-mistake test points it at deliberately broken variants.
+_OVERRIDE = os.environ.get("INPC_ORACLE_LIB")
+_LIB_PATH = _OVERRIDE or os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -38,16 +41,22 @@ class OrcOpts(ct.Structure):
                 ("dilation", ct.c_float), ("n_threads", ct.c_int32)]
 
 
+def compile_command(sources, out):
+    """g++ command line that builds the oracle library from `sources`."""
+    return ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+            "-fno-fast-math", *sources, "-o", out]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle (g++, -ffp-contract=off so FP32 decisions round op by op)."""
+    if _OVERRIDE:
+        return _OVERRIDE
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", *_SRCS, "-o", tmp]
-    subprocess.run(cmd, check=True)
+    subprocess.run(compile_command(_SRCS, tmp), check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 

@@ -95,6 +95,15 @@ def test_wrap_around_seam():
     # every value lies between the two seam columns, both sides are used
     assert np.all(bg > 0.999) and np.all(bg < 3.001)
     assert bg.max() - bg.min() > 1e-4
+    # and each one is the periodic interpolation at its texel coordinate X
+    dw = _world_dirs(cam)
+    X = (np.arctan2(dw[..., 0], dw[..., 2]) / (2 * np.pi) + 0.5) * Wb - 0.5
+    c0 = np.floor(X)
+    a = X - c0
+    col = env[0, :, 0]
+    want = (1 - a) * col[c0.astype(int) % Wb] + a * col[(c0.astype(int) + 1) % Wb]
+    assert np.any(np.abs(X - (Wb - 1)) < 1) or np.any(X < 0)  # the seam is crossed
+    np.testing.assert_allclose(bg[..., 0], want, rtol=0, atol=1e-9)
 
 
 def test_cached_directions_equal_on_the_fly():

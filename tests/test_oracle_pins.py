@@ -399,6 +399,78 @@ def test_adjoint_gaussian_finite_differences(oracle_lib, cov):
     assert np.abs(g["d_xyz"]).max() > 0 and np.abs(g["d_scale"]).max() > 0
 
 
+@pytest.mark.parametrize("pin32", [True, False])
+def test_alpha_clamp_closed_form(oracle_lib, pin32):
+    """A point on a pixel centre with opacity 1 has bilinear weight 1 there, so
+    o w = 1 exceeds alpha_max and the fragment blends with alpha = alpha_max
+    (0.99 as an FP32 parameter): F = alpha_max f and alpha_out = alpha_max.
+    Nothing flows back through a clamped alpha: the opacity gets no gradient,
+    the features get T a g_F = alpha_max g_F."""
+    cam = cam_at(4, 4, 4.0)
+    xyz = np.array([point_at_pixel(cam, 1.5, 2.5, 2.0)])  # centre of pixel (1, 2), exact in FP32
+    o = np.array([1.0])
+    feat = np.array([[0.3, 0.8]])
+    amax = float(np.float32(0.99))
+    r = oracle_lib.render(xyz, o, feat, cam, pin32=pin32)
+    np.testing.assert_allclose(r["F"][2, 1], amax * feat[0], rtol=1e-15)
+    assert abs(r["alpha"][2, 1] - amax) < 1e-15
+    gF = np.zeros((4, 4, 2))
+    gF[2, 1] = [1.0, -2.0]
+    g = oracle_lib.backward(xyz, o, feat, cam, gF, None, None, pin32=pin32)
+    assert g["d_opacity"][0] == 0.0
+    np.testing.assert_allclose(g["d_feat"][0], amax * gF[2, 1], rtol=1e-15)
+
+
+def _rotated(cam, seed):
+    """The same intrinsics with a general rotation and translation."""
+    rng = np.random.default_rng(seed)
+    cam.R = scenes.random_rotations(rng, 1)[0].astype(np.float32)
+    cam.t = rng.uniform(-0.5, 0.5, 3).astype(np.float32)
+    return cam
+
+
+def _to_world(cam, pc):
+    """World points whose camera-space images (x_c = R x_w + t) are pc."""
+    return (np.asarray(pc, np.float64) - cam.t.astype(np.float64)) @ cam.R.astype(np.float64)
+
+
+def test_rotated_camera_projection(oracle_lib):
+    """Pinhole model of Sec. 2 with x_c = R x_w + t for a general rotation:
+    points placed at known camera-space positions land at u = f x_c / z_c + c_x,
+    v = f y_c / z_c + c_y, depth z_c (every other pin uses R = I, where R and
+    R^T cannot be told apart)."""
+    cam = _rotated(cam_at(64, 48, 50.0), 13)
+    rng = np.random.default_rng(13)
+    n = 200
+    z = rng.uniform(1.0, 3.0, n)
+    pc = np.stack([rng.uniform(-0.5, 0.5, n) * z, rng.uniform(-0.4, 0.4, n) * z, z], 1)
+    p = oracle_lib.project(_to_world(cam, pc), cam, pin32=False)
+    assert np.all(p["vis"] == 1)
+    np.testing.assert_allclose(p["uvz"][:, 0], cam.fx * pc[:, 0] / z + cam.cx, rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(p["uvz"][:, 1], cam.fy * pc[:, 1] / z + cam.cy, rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(p["uvz"][:, 2], z, rtol=1e-5)
+
+
+def test_adjoint_gaussian_finite_differences_rotated_camera(oracle_lib):
+    """Position gradients are world-space: with a rotated camera the chain rule
+    carries R^T (finite differences in world coordinates)."""
+    rng = np.random.default_rng(14)
+    v = scenes.random_small_view(14, 40, 24, 20, c=2, gaussian=True, f=30.0)
+    cam = _rotated(v.camera, 14)
+    xyz = _to_world(cam, v.xyz.astype(np.float64))
+    o = rng.uniform(0.2, 0.9, 40)
+    s = v.scale.astype(np.float64) * 5
+    feat = rng.uniform(0, 1, (40, 2))
+    gF, gA, gD = v.g_feat.astype(np.float64), v.g_alpha.astype(np.float64), v.g_depth.astype(np.float64)
+    kw = dict(mode="gaussian", gauss_cov="ewa")
+    g = oracle_lib.backward(xyz, o, feat, cam, gF, gA, gD, scale=s, pin32=False, **kw)
+    an = dict(o=g["d_opacity"], feat=g["d_feat"], xyz=g["d_xyz"], scale=g["d_scale"])
+    params = [("xyz", (i, c)) for i in range(2, 40, 3) for c in range(3)]
+    n = _fd_check(oracle_lib, xyz, o, feat, cam, gF, gA, gD, an, scale=s, params=params, **kw)
+    assert n >= 0.8 * len(params)
+    assert np.abs(g["d_xyz"]).max() > 0
+
+
 def test_eq2_zero_alpha_with_background(oracle_lib):
     """Appendix Eq. 2 for a fragment with alpha_k = 0, background composited
     through the alpha output: F_total = F + T_{K+1} f_bg. The derivative is
