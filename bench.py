@@ -429,6 +429,11 @@ def run_ours(args, ws_, rank, local):
     if not args.no_e2e:
         e2e = run_e2e(args, scene, tens, cviews, opts, wsp, stream, dev, n_points, ws_, dist)
 
+    gauss_extra = None
+    if gauss and rank == 0:
+        gauss_extra = run_gauss_extra(scene, cviews, opts, wsp, lay, n_points, stream, flush,
+                                      max(3, args.steps // 2), do_bwd)
+
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws_,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -449,6 +454,7 @@ def run_ours(args, ws_, rank, local):
         "ring_buffer": ring,
         "untiled_baseline": untiled,
         "contraction": contraction,
+        "gaussian": gauss_extra,
         "blend_fwd_roofline": ({"achieved": blend["gbs"], "peak": peak, "unit": "GB/s",
                                 "frac": round((blend["gbs"] or 0) / peak, 4)} if blend else None),
         "kernels": kernels, "kernel_timing": prof_src, "gpu_launches": gpu_launches,
@@ -456,6 +462,53 @@ def run_ours(args, ws_, rank, local):
         "clocks": clocks, "e2e": e2e,
     }
     return out, dist
+
+
+def run_gauss_extra(scene, cviews, opts, wsp, lay, n_points, stream, flush, reps, do_bwd):
+    """Gaussian workloads: the 3-sigma pixel radii the projection gave the
+    visible points (read from the records of the last timed step, before
+    anything else reuses the workspace), copies per point, and the same step
+    with the isotropic screen-space covariance instead of the EWA one."""
+    import torch
+
+    from paper_2508_19140_gb300 import rast
+
+    torch.cuda.synchronize()
+    words = lay["records"][1] // 4 // max(n_points, 1)
+    off, nb = lay["records"]
+    recs = wsp[off:off + nb].view(torch.int32).view(n_points, words)
+    r = recs[:, 7].view(torch.float32)  # record word 7: radius in pixels
+    coff = lay["count"][0]
+    cnt = wsp[coff:coff + 4 * n_points].view(torch.int32)
+    vis = cnt > 0
+    rv = r[vis].round().clamp(0, 17).to(torch.int64)
+    hist = torch.bincount(rv, minlength=18).tolist()
+    n_vis = int(vis.sum().item())
+    copies = int(cnt[vis].to(torch.int64).sum().item())
+
+    iso = rast.make_opts(mode="gaussian", gauss_cov="iso", tile=int(opts.tile), blend_depth=int(opts.blend_depth))
+    passes = rast.PASS_FWD | (rast.PASS_BWD if do_bwd else 0)
+    for _ in range(2):
+        rast.rasterize_batch(cviews, passes, iso, wsp, stream)
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rast.rasterize_batch(cviews, passes, iso, wsp, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / reps
+    st, stats = rast.rasterize_get_status(wsp, stream)
+    return {"radius_px_hist": {"bins": "r = 0, 1, ..., 16 px; last bin r >= 17", "counts": hist,
+                               "visible_points": n_vis},
+            "copies_per_visible_point": round(copies / max(n_vis, 1), 3),
+            "isotropic_covariance": {"ms_per_step": round(ms, 4),
+                                     "points_per_s": round(n_points / (ms / 1e3), 1),
+                                     "copies": int(stats["n_copies"]), "status": int(st)}}
 
 
 def run_background(scene, tens, dev, stream, flush, peak, reps):
@@ -826,6 +879,11 @@ def main():
         val, npts, dt, desc = oracle_sample(scene, args.cpu_budget_s)
         out["cpu_baseline"] = {"value": round(val, 1), "unit": UNIT, "cores": oracle.num_threads(),
                                "kind": "oracle", "sample": desc, "seconds": round(dt, 2)}
+        if sum(len(v.xyz) for v in scene.views) <= 100_000:
+            # small frames: the oracle on one thread as well (this sets the
+            # oracle's thread count for the rest of the process)
+            v1, _, dt1, _ = oracle_sample(scene, args.cpu_budget_s, threads=1)
+            out["cpu_baseline"]["single_thread"] = {"value": round(v1, 1), "cores": 1, "seconds": round(dt1, 2)}
     elif rank == 0:
         out["cpu_baseline"] = None
     if rank == 0:
