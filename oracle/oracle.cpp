@@ -243,11 +243,6 @@ bool fragment(const Splat& sp, double opac, int px, int py, const orc_opts_t& o,
     return true;
 }
 
-bool fragment_any(const Splat& sp, double opac, int px, int py, const orc_opts_t& o, Frag& fr) {
-    return o.pin32 ? fragment<float>(sp, opac, px, py, o, fr)
-                   : fragment<double>(sp, opac, px, py, o, fr);
-}
-
 struct Ctx {
     int64_t n;
     const double* xyz;

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     const ViewDev& V = vt.v[view_of_tile(vt, tile)];
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int lx = tid & (TS - 1), ly = tid / TS;
     const int px = tx * TS + lx, py = ty * TS + ly;
     const bool inside = px < V.W && py < V.H;

@@ -63,20 +63,6 @@ __device__ __forceinline__ void load_u32s(const uint32_t* __restrict__ p, int64_
     }
 }
 
-__device__ __forceinline__ void load_rects(const uint2* __restrict__ p, int64_t s0, int64_t n, uint2 r[kPer]) {
-    if (s0 + kPer <= n) {
-#pragma unroll
-        for (int j = 0; j < kPer; j += 2) {
-            const uint4 q = *reinterpret_cast<const uint4*>(p + s0 + j);
-            r[j] = make_uint2(q.x, q.y);
-            r[j + 1] = make_uint2(q.z, q.w);
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) r[j] = s0 + j < n ? p[s0 + j] : make_uint2(1u, 0u);
-    }
-}
-
 __device__ __forceinline__ void store_rects(uint2* __restrict__ p, int64_t s0, int64_t n, const uint2 r[kPer]) {
     if (s0 + kPer <= n) {
 #pragma unroll
