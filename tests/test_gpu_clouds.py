@@ -9,7 +9,7 @@ import torch
 import oracle
 from paper_2508_19140_gb300 import rast, scenes
 
-from gpu_util import Run, bf16_round
+from gpu_util import Run
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"

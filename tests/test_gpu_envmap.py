@@ -9,7 +9,6 @@ than 1e-5 relative, the image bar used everywhere else. dL/dalpha follows the
 same bound. The map gradient sums w (1 - alpha) g over pixels with weights
 that move by the same ~3e-4 texel: normwise 1e-3 of the gradient, and exact
 integer (fixed-point) accumulation makes reruns bit-identical."""
-import math
 
 import numpy as np
 import pytest

@@ -2,7 +2,6 @@
 views with no data collective (the shards partition the views, balanced by
 point count), derive distinct per-rank frame seeds for weak scaling, and
 agree on the max-over-ranks step time the benchmark reports."""
-import os
 import socket
 
 import pytest
