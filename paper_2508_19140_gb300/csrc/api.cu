@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rast_internal.cuh"
 
 namespace rast {
@@ -310,6 +312,7 @@ Profiler g_prof;
 }  // namespace
 
 ProfScope::ProfScope(const char* name, cudaStream_t st) : idx(-1), s(st) {
+    nvtxRangePushA(name);  // a no-op unless a profiler is attached
     std::lock_guard<std::mutex> lk(g_prof.mu);
     if (!g_prof.on) return;
     ProfRec r{name, g_prof.get(), g_prof.get()};
@@ -319,6 +322,7 @@ ProfScope::ProfScope(const char* name, cudaStream_t st) : idx(-1), s(st) {
 }
 
 ProfScope::~ProfScope() {
+    nvtxRangePop();
     if (idx < 0) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     if (idx < (int)g_prof.recs.size()) cudaEventRecord(g_prof.recs[idx].b, s);

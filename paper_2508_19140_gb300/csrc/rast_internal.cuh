@@ -143,7 +143,9 @@ __device__ __forceinline__ uint32_t rect_count(uint2 r) {
 }
 
 // ---- per-kernel profiling (defined in api.cu) ------------------------------
-// While profiling is enabled, records a CUDA event pair on `s` around the
+// Opens an NVTX range named `name` for the scope (host-side, so profilers can
+// group the launches by stage; free when no profiler is attached). While
+// profiling is enabled it also records a CUDA event pair on `s` around the
 // scope; rasterize_profile_read() sums the times per name. `name` must have
 // static storage duration.
 struct ProfScope {
