@@ -30,8 +30,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "splatted points/s (fwd+bwd) at 1280x832"
 UNIT = "points/s"
+
+
+def metric_label(scene):
+    """The headline metric for this workload: splatted points/s of the pass it
+    runs, at its image size (several views: their count and size range)."""
+    pas = "fwd+bwd" if scene.backward else "fwd"
+    sizes = sorted({(v.camera.width, v.camera.height) for v in scene.views}, key=lambda s: s[0] * s[1])
+    if len(scene.views) == 1:
+        where = f"at {sizes[0][0]}x{sizes[0][1]}"
+    else:
+        where = (f"over {len(scene.views)} views of {sizes[0][0]}x{sizes[0][1]} to "
+                 f"{sizes[-1][0]}x{sizes[-1][1]}")
+    mode = "" if scene.mode == "bilinear" else ", Gaussian splats"
+    return f"splatted points/s ({pas}{mode}) {where}"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 
@@ -48,6 +61,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bg", action="store_true", help="skip the background-model measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the per-output error measurement against the FP64 oracle")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--graph", type=int, default=-1,
                     help="time CUDA-graph replays of the step (default: on for the batched 8-view workload)")
@@ -315,7 +330,9 @@ def run_ours(args, ws_, rank, local):
     if sampler:
         sampler.start()
         time.sleep(0.3)
-    rast.rasterize_profile_enable(graph is None)
+    # The timed region runs the bare product call (no per-kernel events);
+    # per-kernel times come from a separate pass right after it.
+    rast.rasterize_profile_enable(False)
     evs = []
     for _ in range(args.steps):
         flush.zero_()
@@ -329,8 +346,6 @@ def run_ours(args, ws_, rank, local):
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
-    prof = rast.rasterize_profile_read()
-    rast.rasterize_profile_enable(False)
     st, stats = rast.rasterize_get_status(wsp, stream)  # counters of the last fwd+bwd step
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
     if dist:
@@ -341,16 +356,19 @@ def run_ours(args, ws_, rank, local):
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
 
-    prof_src = "live CUDA events around each kernel in the timed region"
-    if graph is not None:
-        rast.rasterize_profile_enable(True)
-        for _ in range(max(3, args.steps // 2)):
-            flush.zero_()
-            step()
-        torch.cuda.synchronize()
-        prof = rast.rasterize_profile_read()
-        rast.rasterize_profile_enable(False)
-        prof_src = "CUDA events around each kernel in non-graph steps right after the graph-timed region"
+    # Per-kernel times: CUDA events on the launch stream around every kernel,
+    # in non-graph steps run right after the timed region (L2 flushed before
+    # each step as in the timed region).
+    prof_steps = max(3, args.steps // 2)
+    rast.rasterize_profile_enable(True)
+    for _ in range(prof_steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    prof = rast.rasterize_profile_read()
+    rast.rasterize_profile_enable(False)
+    prof_src = ("CUDA events around each kernel on the launch stream, in non-graph steps right after "
+                "the timed region (the timed region itself records no per-kernel events)")
 
     seq = None
     if len(scene.views) > 1 and bf16 and rank == 0:
@@ -409,7 +427,6 @@ def run_ours(args, ws_, rank, local):
                     "algorithmic_bytes": k["bytes"],
                     "peak_source": f"{peak_src} (hbm_gbs, copy burst)"}
     blend = kernels.get("blend_fwd")
-    prof_steps = args.steps if graph is None else max(3, args.steps // 2)
     gpu_launches = int(round(sum(x[0] for x in prof.values()) / max(prof_steps, 1) * args.steps))
 
     bg = None
@@ -429,13 +446,17 @@ def run_ours(args, ws_, rank, local):
     if not args.no_e2e:
         e2e = run_e2e(args, scene, tens, cviews, opts, wsp, stream, dev, n_points, ws_, dist)
 
+    accuracy = None
+    if not args.no_accuracy and rank == 0:
+        accuracy = run_accuracy(scene, dev, opts)
+
     gauss_extra = None
     if gauss and rank == 0:
         gauss_extra = run_gauss_extra(scene, cviews, opts, wsp, lay, n_points, stream, flush,
                                       max(3, args.steps // 2), do_bwd)
 
     out = {
-        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws_,
+        "metric": metric_label(scene), "value": round(value, 1), "unit": UNIT, "n_gpus": ws_,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16-features/f32" if bf16 else "f32", "data": "synthetic",
@@ -459,7 +480,7 @@ def run_ours(args, ws_, rank, local):
                                 "frac": round((blend["gbs"] or 0) / peak, 4)} if blend else None),
         "kernels": kernels, "kernel_timing": prof_src, "gpu_launches": gpu_launches,
         "graph": graph is not None, "batched_vs_sequential": seq,
-        "clocks": clocks, "e2e": e2e,
+        "clocks": clocks, "e2e": e2e, "accuracy": accuracy,
     }
     return out, dist
 
@@ -792,6 +813,124 @@ def run_e2e(args, scene, tens, cviews, opts, wsp, stream, dev, n_points, ws_, di
                    "overlap step k's kernels on two copy streams"}
 
 
+# ----------------------------------------------------------------------------- accuracy
+
+def _err_stats(got, want, mask=None):
+    """Max relative error over elements with |ref| above 1e-3 of the largest,
+    normwise relative error, and max absolute error of `got` against `want`."""
+    g = np.asarray(got, np.float64)
+    w = np.asarray(want, np.float64)
+    if mask is not None:
+        g, w = g[mask], w[mask]
+    if w.size == 0:
+        return None
+    d = np.abs(g - w)
+    big = np.abs(w) > 1e-3 * max(np.abs(w).max(), 1e-30)
+    return {"max_rel": float((d[big] / np.abs(w[big])).max()) if big.any() else 0.0,
+            "norm_rel": float(np.linalg.norm(g - w) / max(np.linalg.norm(w), 1e-30)),
+            "max_abs": float(d.max())}
+
+
+def run_accuracy(scene, dev, opts, n_pix=2000, n_pts=400, seed=7):
+    """Measured error of every output against the FP64 oracle, with FP32 and
+    with BF16 features, on sampled pixels (F, alpha, depth) and sampled points
+    (d_feat, d_opacity, and in Gaussian mode d_xyz, d_scale) of the
+    workload's first and last views. BF16 runs are compared with the oracle
+    fed the same BF16-rounded features (accumulation error) and with the
+    oracle fed the FP32 features (total error). Gaussian pixels whose
+    termination decision lies within 1e-5 of t_min (CPU and GPU exp can
+    differ by an ulp there), and points touching them, are left out and
+    counted."""
+    import torch
+
+    import oracle
+    from paper_2508_19140_gb300 import rast
+
+    oracle.build()
+    gauss = scene.mode == "gaussian"
+    kw = dict(mode=scene.mode, tile=16, pin32=True)
+    vids = sorted({0, len(scene.views) - 1})
+    res = {"what": f"sampled {n_pix} pixels and {n_pts} points per view, views {vids}, "
+                   "errors vs the FP64 oracle", "tile": int(opts.tile),
+           "blend_depth": int(opts.blend_depth) or int(opts.tile) ** 2}
+    for bf16 in (False, True):
+        tens, cviews = make_views(scene, dev, bf16)
+        ws = torch.empty(rast.rasterize_workspace_size(cviews, opts), dtype=torch.uint8, device=dev)
+        passes = rast.PASS_FWD | (rast.PASS_BWD if scene.backward else 0)
+        rast.rasterize_batch(cviews, passes, opts, ws)
+        st, _ = rast.rasterize_get_status(ws)
+        torch.cuda.synchronize()
+        acc = {}
+        excluded = 0
+        for k in vids:
+            v, t = scene.views[k], tens[k]
+            rng = np.random.default_rng(seed + k)
+            W, H = v.camera.width, v.camera.height
+            pix = rng.choice(W * H, min(n_pix, W * H), replace=False)
+            feats = {"same_features": v.feat if not bf16 else
+                     torch.from_numpy(v.feat).to(torch.bfloat16).float().numpy()}
+            if bf16:
+                feats["fp32_features"] = v.feat
+            scale = v.scale if gauss else None
+            F = t["F"].cpu().numpy().reshape(-1, v.feat.shape[1])[pix]
+            A = t["A"].cpu().numpy().reshape(-1)[pix]
+            D = t["D"].cpu().numpy().reshape(-1)[pix]
+            pm = np.zeros(len(v.xyz), np.uint8)
+            pm[rng.choice(len(v.xyz), min(n_pts, len(v.xyz)), replace=False)] = 1
+            if gauss and scene.backward:
+                p = oracle.project(v.xyz, v.camera, scale=scale, **kw)
+                boxes = {}
+                for i in np.nonzero(pm & (p["vis"] == 1))[0]:
+                    x0, x1, y0, y1 = p["box"][i]
+                    boxes[i] = (np.arange(y0, y1 + 1)[:, None] * W + np.arange(x0, x1 + 1)[None, :]).ravel()
+                if boxes:
+                    allpix = np.unique(np.concatenate(list(boxes.values())))
+                    marg = oracle.render(v.xyz, v.opacity, feats["same_features"], v.camera, scale=scale,
+                                         pix=allpix, **kw)["margin"]
+                    amb = set(allpix[marg <= 1e-5].tolist())
+                    for i, px in boxes.items():
+                        if amb.intersection(px.tolist()):
+                            pm[i] = 0
+                            excluded += 1
+            got_g = None
+            if scene.backward:
+                got_g = {"d_feat": t["d_feat"].cpu().numpy(), "d_opacity": t["d_op"].cpu().numpy()}
+                if gauss:
+                    got_g["d_xyz"] = t["d_xyz"].cpu().numpy()
+                    if t.get("d_scale") is not None:
+                        got_g["d_scale"] = t["d_scale"].cpu().numpy()
+            sel = pm == 1
+            for ref_kind, fv in feats.items():
+                ref = oracle.render(v.xyz, v.opacity, fv, v.camera, scale=scale, pix=pix, **kw)
+                ok = ref["margin"] > 1e-5 if gauss else np.ones(len(pix), bool)
+                if ref_kind == "same_features":
+                    excluded += int((~ok).sum())
+                outs = {"F": (F, ref["F"], ok[:, None] & np.ones_like(F, bool)),
+                        "alpha": (A, ref["alpha"], ok), "depth": (D, ref["depth"], ok)}
+                if got_g is not None:
+                    g = oracle.backward(v.xyz, v.opacity, fv, v.camera, v.g_feat, v.g_alpha, v.g_depth,
+                                        scale=scale, pmask=pm, **kw)
+                    for key, val in got_g.items():
+                        outs[key] = (val[sel], g[key][sel], None)
+                for key, (got, want, m) in outs.items():
+                    acc.setdefault(ref_kind, {}).setdefault(key, []).append((got, want, m))
+        dres = {}
+        for ref_kind, per in acc.items():
+            dres[ref_kind] = {}
+            for key, items in per.items():
+                got = np.concatenate([np.asarray(a).reshape(len(a), -1) for a, _, _ in items])
+                want = np.concatenate([np.asarray(b).reshape(len(b), -1) for _, b, _ in items])
+                masks = [np.ones_like(np.asarray(a).reshape(len(a), -1), bool) if m is None else
+                         np.asarray(m).reshape(len(a), -1) for a, _, m in items]
+                dres[ref_kind][key] = _err_stats(got, want, np.concatenate(masks))
+        dres["status"] = int(st)
+        res["bf16" if bf16 else "fp32"] = dres
+        del tens, cviews, ws
+        torch.cuda.empty_cache()
+    res["excluded_termination_ambiguous"] = excluded
+    return res
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def oracle_sample(scene, budget_s, threads=0, pin32=True):
@@ -852,7 +991,7 @@ def run_reference(args, rank):
     tot_t = sum(x[1] for x in vals)
     value = tot_pts / tot_t
     cores = oracle.num_threads()
-    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
+    return {"impl": "reference", "metric": metric_label(scene), "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot_t / steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",

@@ -27,8 +27,10 @@
  *     f32 or bf16 (row-major), images [H][W][C] f32 (HWC, as F in Sec. 2),
  *     alpha and depth [H][W] f32.
  *   - Errors: no C++ exception crosses this ABI and no kernel traps. A
- *     device-side capacity overflow is recorded in the workspace and reported
- *     by rasterize_get_status().
+ *     device-side capacity overflow, or a bounded device-side wait that ran
+ *     out, is recorded in the workspace and reported by
+ *     rasterize_get_status(); the stages after it then see an empty copy list,
+ *     so no kernel reads a partial sort result.
  */
 #ifndef INPC_RAST_H
 #define INPC_RAST_H
@@ -90,8 +92,19 @@ typedef struct {
     float alpha_max;       /* alpha clamp (0.99) */
     float dilation;        /* screen-space dilation variance, Gaussian mode (0.16) */
     int32_t max_copies;    /* capacity: point-tile copies per point (0 = 4 bilinear, 16 Gaussian) */
-    int32_t flags;         /* reserved, 0 */
+    int32_t flags;         /* 0, or RAST_FLAG_TEST_SORT_STALL (testing the failure path only) */
 } rast_opts_t;
+
+/* Test hook for the bounded device-side waits (failure detection). With this
+ * flag the first digit pass of the depth sort withholds the look-back word of
+ * its first 4096-key tile, so the tile after it waits on a word nothing will
+ * ever set, and that wait is limited to 64 polls instead of 2^22. The wait
+ * runs out, the kernel sets the timeout bit of the workspace error word and
+ * returns normally; every later stage sees the bit and produces an empty copy
+ * list (images of zero coverage, zero point gradients), and
+ * rasterize_get_status() returns RAST_ERR_TIMEOUT. Needs more than 4096
+ * points. Never set outside tests. */
+#define RAST_FLAG_TEST_SORT_STALL 1
 
 typedef struct {
     float* feat;    /* [H][W][C] out */
@@ -128,6 +141,9 @@ typedef struct {
     int64_t n_pixels;
     int64_t needed_records_bwd; /* records the backward replay read (last backward) */
 } rast_stats_t;
+
+/* One workspace array: name, byte offset, bytes (rasterize_workspace_layout). */
+typedef struct { char name[24]; int64_t offset; int64_t bytes; } rast_ws_entry_t;
 
 /* One row of the per-stage timing profile. */
 typedef struct {
@@ -168,10 +184,23 @@ rast_status_t rasterize_fwd(const rast_points_t* pts, const rast_camera_t* cam,
  * finds the previous call's contents there (the forward clears what it needs
  * zeroed); calls whose GPU work overlaps race on it and must be serialised by
  * the caller. Writes out->feat, out->alpha, out->depth; no backward state is
- * kept for the caller. */
+ * kept for the caller. Outside stream capture every call looks the array's
+ * address up again (a context torn down and created again gets the new one);
+ * during capture the address found by the last call outside it is used.
+ * Errors the GPU raises during the pass (copies beyond max_copies, a bounded
+ * wait that ran out) are not in the return value, which comes before the GPU
+ * work: read them with rasterize_noalloc_get_status. */
 rast_status_t rasterize_fwd_noalloc(const rast_points_t* pts, const rast_camera_t* cam,
                                    const rast_opts_t* opts, const rast_images_t* out,
                                    void* stream);
+
+/* Synchronises `stream`, then reads the device-side status word and counters
+ * that the last rasterize_fwd_noalloc call on the current device left in the
+ * static array (stats may be NULL), as rasterize_get_status does for a
+ * caller's workspace. No counterpart in the paper. Before any
+ * rasterize_fwd_noalloc call on the device it returns RAST_OK with zero
+ * counters. */
+rast_status_t rasterize_noalloc_get_status(void* stream, rast_stats_t* stats);
 
 /* Backward pass of ONE view (appendix Eq. 2, corrected). `workspace` must
  * hold the state of the matching rasterize_fwd on the same inputs. Writes
@@ -202,6 +231,33 @@ size_t rasterize_untiled_workspace_size(const rast_points_t* pts, const rast_cam
                                         const rast_opts_t* opts);
 rast_status_t rasterize_fwd_untiled(const rast_points_t* pts, const rast_camera_t* cam, const rast_opts_t* opts,
                                     void* workspace, size_t ws_bytes, const rast_images_t* out, void* stream);
+
+/* Untiled baseline in the arrangement whose sort cost Sec. 3.2 "Tiled
+ * Rendering" counts as 28n: every point makes one copy per in-image pixel of
+ * its 2x2 footprint (about 4n copies), written in point order, and ONE stable
+ * LSD radix sort orders the copies by a 64-bit key [pixel id | depth key]
+ * (pixel id in the high word, the FP32 depth bits minus those of near_z in
+ * the low word; ties fall back to point index). The digit passes over the low
+ * word carry each copy's id; before the passes over the high word, each
+ * copy's pixel id and point index are fetched by that id (the key's high word
+ * is only read once its digits are reached). Each pixel's list is then
+ * composited by one warp: 32 fragments' records gathered and their alphas
+ * computed at once, the transmittance stepped through them in list order with
+ * the same FP32 operations as the per-thread walk (so the per-pixel lists,
+ * last-contributor positions and termination decisions equal
+ * rasterize_fwd_untiled's bit for bit), the sums of the chunk reduced across
+ * the warp (images within FP32 rounding of the serial sums). Forward only,
+ * bilinear only (RAST_ERR_NOT_SUPPORTED otherwise); opts->tile and
+ * blend_depth are ignored. Workspace, stream and errors as rasterize_fwd.
+ * rasterize_untiled64_workspace_layout lists the workspace arrays like
+ * rasterize_workspace_layout ("sorted_keys" = pixel ids, "sorted_vals" =
+ * point indices in (pixel, depth, point index) order). */
+size_t rasterize_untiled64_workspace_size(const rast_points_t* pts, const rast_camera_t* cam,
+                                          const rast_opts_t* opts);
+int32_t rasterize_untiled64_workspace_layout(const rast_points_t* pts, const rast_camera_t* cam,
+                                             const rast_opts_t* opts, rast_ws_entry_t* out, int32_t max);
+rast_status_t rasterize_fwd_untiled64(const rast_points_t* pts, const rast_camera_t* cam, const rast_opts_t* opts,
+                                      void* workspace, size_t ws_bytes, const rast_images_t* out, void* stream);
 
 /* Several point clouds rendered into ONE image (the ring buffer of
  * view-specific clouds of Sec. 3.1 "Fast and Stable View-Specific Sampling
@@ -236,7 +292,6 @@ const char* rasterize_status_string(rast_status_t status);
  * "sorted_vals" (tile id and point index of every copy, in (tile, depth bits,
  * point index) order). Writes up to `max` (name, offset, bytes) triples and
  * returns how many exist. Layout only: no device access. */
-typedef struct { char name[24]; int64_t offset; int64_t bytes; } rast_ws_entry_t;
 int32_t rasterize_workspace_layout(const rast_view_t* views, int32_t n_views,
                                    const rast_opts_t* opts, rast_ws_entry_t* out, int32_t max);
 

@@ -40,12 +40,20 @@ int bit_length(uint64_t x) {
 enum Slot {
     S_HDR, S_REC, S_RECT, S_CNT, S_ZBITS, S_KEYA0, S_KEYA1, S_VALA0, S_VALA1, S_RECTS, S_BASE, S_BLK,
     S_KEYC0, S_KEYC1, S_VALC0, S_VALC1, S_PARTIAL, S_GROW, S_SGHIST, S_SCOUNT, S_SSTATUS, S_RANGES, S_ORDER, S_CUTOFF, S_TRACE,
-    S_TFINAL, S_LAST, S_COUNT
+    S_TFINAL, S_LAST, S_PIXC, S_PTC, S_COUNT
 };
 const char* kSlotNames[S_COUNT] = {
     "header", "records", "rect", "count", "zbits", "keys_a0", "keys_a1", "vals_a0", "vals_a1",
     "rect_sorted", "base", "block_sums", "keys_c0", "keys_c1", "vals_c0", "vals_c1",
-    "partial", "grad_rows", "sort_hist", "sort_counters", "sort_status", "ranges", "tile_order", "cutoff", "tile_trace", "t_final", "last"};
+    "partial", "grad_rows", "sort_hist", "sort_counters", "sort_status", "ranges", "tile_order", "cutoff", "tile_trace", "t_final", "last",
+    "copy_pixel", "copy_point"};
+
+// Arrangements of the pipeline.
+enum Arrangement {
+    kTiled = 0,        // tiles of opts->tile pixels, split sort (the paper's method)
+    kUntiledSplit = 1, // one-pixel tiles through the split sort, one thread per pixel
+    kUntiledKey64 = 2  // one-pixel tiles, one 64-bit [pixel | depth] key sort of copies, one warp per pixel
+};
 
 struct Plan {
     ViewTable vt;
@@ -55,7 +63,10 @@ struct Plan {
     int64_t copy_cap, blk_cap;
     SortPlan planA, planC;
     int partial_floats;
+    int arrangement;
 };
+
+int32_t write_layout(const Plan& pl, int keys_slot, int vals_slot, rast_ws_entry_t* out, int32_t max);
 
 rast_status_t check_view(const rast_view_t& v, int pass, int T) {
     const rast_points_t& p = v.pts;
@@ -84,9 +95,11 @@ bool blend_depth_supported(int mode, int tile, int depth) {
 
 // cont[k] != 0: view k is another point cloud of view k - 1's image (same
 // camera, outputs and image gradients; its points join the same tile lists).
-// untiled: one "tile" per pixel (per-pixel lists, the untiled baseline).
+// arrangement: see Arrangement (the untiled ones have one "tile" per pixel:
+// per-pixel lists, the untiled baselines).
 rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_opts_t* o, int pass,
-                        Plan& pl, const uint8_t* cont = nullptr, bool untiled = false) {
+                        Plan& pl, const uint8_t* cont = nullptr, int arrangement = kTiled) {
+    const bool untiled = arrangement != kTiled;
     if (!views || !o || n_views < 1 || n_views > kMaxViews) return RAST_ERR_ARG;
     if (o->mode != RAST_SPLAT_BILINEAR && o->mode != RAST_SPLAT_GAUSSIAN) return RAST_ERR_ARG;
     if (o->gauss_cov != RAST_GAUSS_EWA && o->gauss_cov != RAST_GAUSS_ISO_SCREEN) return RAST_ERR_ARG;
@@ -97,12 +110,14 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     if (!untiled && !blend_depth_supported(o->mode, o->tile, depth)) return RAST_ERR_NOT_SUPPORTED;
     if (!(o->t_min >= 0.f) || !(o->alpha_max > 0.f && o->alpha_max < 1.f)) return RAST_ERR_ARG;
     if (!(o->dilation >= 0.f) || o->max_copies < 0) return RAST_ERR_ARG;
+    if ((o->flags & ~RAST_FLAG_TEST_SORT_STALL) != 0) return RAST_ERR_ARG;
     const int C = views[0].pts.channels;
     const int dt = views[0].pts.feat_dtype;
     if (dt != RAST_F32 && dt != RAST_BF16) return RAST_ERR_ARG;
     if (C < 1) return RAST_ERR_ARG;
     if (!channels_supported(C)) return RAST_ERR_NOT_SUPPORTED;
     std::memset(&pl, 0, sizeof(pl));
+    pl.arrangement = arrangement;
     ViewTable& vt = pl.vt;
     vt.n_views = n_views;
     vt.C = C;
@@ -114,6 +129,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     vt.t_min = o->t_min;
     vt.alpha_max = o->alpha_max;
     vt.dilation = o->dilation;
+    vt.flags = o->flags;
     vt.feat_word = o->mode == RAST_SPLAT_GAUSSIAN ? 8 : 4;
     // Power-of-two record stride of at least 8 words (see RecLayout).
     const int fwords = vt.bf16 ? (C + 1) / 2 : C;
@@ -210,9 +226,12 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     pl.bytes[S_SGHIST] = (size_t)kMaxSortPasses * 512 * 4;
     pl.bytes[S_SCOUNT] = (size_t)kMaxSortPasses * 4;
     {
-        const int64_t wa = sort_status_words(pl.planA, npt), wc = sort_status_words(pl.planC, pl.copy_cap);
+        // The 64-bit-key arrangement sorts copies, not points, by depth.
+        const int64_t na = arrangement == kUntiledKey64 ? pl.copy_cap : npt;
+        const int64_t wa = sort_status_words(pl.planA, na), wc = sort_status_words(pl.planC, pl.copy_cap);
         pl.bytes[S_SSTATUS] = (size_t)(wa > wc ? wa : wc) * 4;
     }
+    pl.bytes[S_PIXC] = pl.bytes[S_PTC] = arrangement == kUntiledKey64 ? (size_t)D * 4 : 0;
     pl.bytes[S_RANGES] = (size_t)ntile * 8;
     pl.bytes[S_ORDER] = (size_t)(ntile + 66) * 4;  // heavy-first order + bucket counts and cursors
     pl.bytes[S_CUTOFF] = (size_t)ntile * 8;
@@ -264,6 +283,8 @@ Bufs make_bufs(const Plan& pl, void* ws) {
     b.trace = (unsigned long long*)at(S_TRACE);
     b.t_final = (float*)at(S_TFINAL);
     b.last = (uint32_t*)at(S_LAST);
+    b.pixC = (uint32_t*)at(S_PIXC);
+    b.ptC = (uint32_t*)at(S_PTC);
     b.copy_cap = pl.copy_cap;
     b.blk_cap = pl.blk_cap;
     return b;
@@ -311,6 +332,19 @@ Profiler g_prof;
 
 }  // namespace
 
+int device_sm_count() {
+    static PerDevice pd;
+    int n = 1;
+    const cudaError_t e = per_device(pd, &n, [](int dev, int* v) {
+        *v = 1;
+        int c = 0;
+        const cudaError_t r = cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        if (r == cudaSuccess && c > 0) *v = c;
+        return cudaSuccess;
+    });
+    return e == cudaSuccess && n > 0 ? n : 1;
+}
+
 ProfScope::ProfScope(const char* name, cudaStream_t st) : idx(-1), s(st) {
     nvtxRangePushA(name);  // a no-op unless a profiler is attached
     std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -353,12 +387,15 @@ cudaError_t run_fwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
     {
         uint32_t* k[2] = {b.keyA[0], b.keyA[1]};
         uint32_t* v[2] = {b.valA[0], b.valA[1]};
-        const SortScratch sc{b.sort_ghist, b.sort_counters, b.sort_status, &b.hdr->error};
+        const SortScratch sc{b.sort_ghist, b.sort_counters, b.sort_status, &b.hdr->error,
+                             (vt.flags & RAST_FLAG_TEST_SORT_STALL) != 0};
         // Only the depth order of the point indices is used after this sort.
         RAST_TRY(radix_sort(k, v, vt.n_total, nullptr, vt.n_total, pl.planA, sc, s, &ra, kDepthSortNames,
                             true, false));
     }
     const uint32_t* depth_sorted = b.valA[ra];
+    // A depth sort whose look-back wait ran out leaves a partial order: the
+    // duplication then sees the error bit and writes no copies.
     RAST_TRY(launch_duplicate(vt, b, depth_sorted, s));
     {
         uint32_t* k[2] = {b.keyC[0], b.keyC[1]};
@@ -371,6 +408,57 @@ cudaError_t run_fwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
     RAST_TRY(launch_tile_order(vt, b, s));
     RAST_TRY(launch_blend_fwd(vt, b, b.valC[rc], s));
     return cudaSuccess;
+}
+
+// Untiled baseline with ONE stable LSD radix sort over the copies' 64-bit key
+// [pixel id | depth key] (ties: point index), the arrangement whose cost
+// Sec. 3.2 "Tiled Rendering" counts as 28n: every point makes a copy per
+// in-image pixel of its 2x2 box (about 4n copies), written in point order.
+// The LSD passes over the low word (depth digits) carry the copy id; before
+// the passes over the high word (pixel digits) each copy's high word and point
+// index are fetched by that id, and those passes carry the point index. The
+// key the passes see is the same 64-bit key digit for digit; only its high
+// word is read when its digits are reached. Result: (pixel, point) pairs in
+// (pixel, depth, point index) order in keys/vals[result_pair(pl)].
+int key64_result_pair(const Plan& pl) {
+    const int ga = pl.planA.passes & 1;  // pair holding the low-word passes' copy ids
+    const int g = ga ^ 1;                // the free pair the gather fills
+    return g ^ (pl.planC.passes & 1);
+}
+
+cudaError_t run_fwd_key64(const Plan& pl, const Bufs& b, cudaStream_t s) {
+    const ViewTable& vt = pl.vt;
+    {
+        ProfScope ps("init_header", s);
+        k_init_header<<<1, 1, 0, s>>>(b.hdr, vt.n_views, vt.n_total, pl.copy_cap, vt.tiles_total,
+                                      vt.pix_total);
+        RAST_TRY(cudaGetLastError());
+    }
+    RAST_TRY(launch_project(vt, b, false, s));
+    RAST_TRY(launch_untiled_copies(vt, b, b.keyA[0], b.keyC[0], b.pixC, b.ptC, s));
+    const SortScratch sc{b.sort_ghist, b.sort_counters, b.sort_status, &b.hdr->error,
+                         (vt.flags & RAST_FLAG_TEST_SORT_STALL) != 0};
+    static const char* const kLoNames[2] = {"sort64.lo.hist", "sort64.lo.sweep"};
+    static const char* const kHiNames[2] = {"sort64.hi.hist", "sort64.hi.sweep"};
+    int ra = 0, rb = 0;
+    {
+        uint32_t* k[2] = {b.keyC[0], b.keyC[1]};
+        uint32_t* v[2] = {b.valC[0], b.valC[1]};
+        // Low word: the values are the copy ids (generated by the first pass).
+        RAST_TRY(radix_sort(k, v, 0, &b.hdr->n_copies, pl.copy_cap, pl.planA, sc, s, &ra, kLoNames, true, false));
+    }
+    const int g = ra ^ 1;
+    RAST_TRY(launch_gather_hi(b, b.valC[ra], b.pixC, b.ptC, b.keyC[g], b.valC[g], s));
+    {
+        uint32_t* k[2] = {b.keyC[g], b.keyC[ra]};
+        uint32_t* v[2] = {b.valC[g], b.valC[ra]};
+        SortScratch sc2 = sc;
+        sc2.stall_test = false;
+        RAST_TRY(radix_sort(k, v, 0, &b.hdr->n_copies, pl.copy_cap, pl.planC, sc2, s, &rb, kHiNames));
+    }
+    const int r = key64_result_pair(pl);
+    RAST_TRY(launch_ranges(vt, b, b.keyC[r], s));
+    return launch_blend_fwd_pixel_warp(vt, b, b.valC[r], s);
 }
 
 cudaError_t run_bwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
@@ -397,17 +485,18 @@ rast_view_t single_view(const rast_points_t* pts, const rast_camera_t* cam, cons
 // One launch sequence over the views (cont: see make_plan).
 rast_status_t run_views(const rast_view_t* views, int32_t n_views, int32_t pass, const rast_opts_t* opts,
                         void* workspace, size_t ws_bytes, void* stream, const uint8_t* cont,
-                        bool untiled = false) {
+                        int arrangement = kTiled) {
     if (pass < 1 || pass > 3) return RAST_ERR_ARG;
     Plan pl;
-    const rast_status_t st = make_plan(views, n_views, opts, pass, pl, cont, untiled);
+    const rast_status_t st = make_plan(views, n_views, opts, pass, pl, cont, arrangement);
     if (st != RAST_OK) return st;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return RAST_ERR_ARG;
     if (ws_bytes < pl.total) return RAST_ERR_CAPACITY;
     Bufs b = make_bufs(pl, workspace);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (pass & RAST_PASS_FWD) {
-        if (run_fwd(pl, b, s) != cudaSuccess) return RAST_ERR_CUDA;
+        const cudaError_t e = arrangement == kUntiledKey64 ? run_fwd_key64(pl, b, s) : run_fwd(pl, b, s);
+        if (e != cudaSuccess) return RAST_ERR_CUDA;
     }
     if (pass & RAST_PASS_BWD) {
         if (run_bwd(pl, b, s) != cudaSuccess) return RAST_ERR_CUDA;
@@ -446,11 +535,24 @@ int32_t rasterize_workspace_layout(const rast_view_t* views, int32_t n_views, co
                                    rast_ws_entry_t* out, int32_t max) {
     Plan pl;
     if (make_plan(views, n_views, opts, 0, pl) != RAST_OK) return -1;
-    const int ra = pl.planA.passes & 1, rc = pl.planC.passes & 1;
+    const int rc = pl.planC.passes & 1;
+    return write_layout(pl, rc ? S_KEYC1 : S_KEYC0, rc ? S_VALC1 : S_VALC0, out, max);
+}
+
+}  // extern "C"
+
+namespace rast {
+namespace {
+
+// Every workspace array as (name, offset, bytes), then the aliases of the
+// sort results: "depth_sorted" (point indices in depth order), "sorted_keys"
+// and "sorted_vals" (the slots given).
+int32_t write_layout(const Plan& pl, int keys_slot, int vals_slot, rast_ws_entry_t* out, int32_t max) {
+    const int ra = pl.planA.passes & 1;
     struct Alias { const char* name; int slot; };
     const Alias extra[] = {{"depth_sorted", ra ? S_VALA1 : S_VALA0},
-                           {"sorted_keys", rc ? S_KEYC1 : S_KEYC0},
-                           {"sorted_vals", rc ? S_VALC1 : S_VALC0}};
+                           {"sorted_keys", keys_slot},
+                           {"sorted_vals", vals_slot}};
     int n = 0;
     for (int k = 0; k < S_COUNT; ++k, ++n) {
         if (out && n < max) {
@@ -469,6 +571,11 @@ int32_t rasterize_workspace_layout(const rast_view_t* views, int32_t n_views, co
     }
     return n;
 }
+
+}  // namespace
+}  // namespace rast
+
+extern "C" {
 
 rast_status_t rasterize_batch(const rast_view_t* views, int32_t n_views, int32_t pass,
                               const rast_opts_t* opts, void* workspace, size_t ws_bytes,
@@ -540,7 +647,7 @@ size_t rasterize_untiled_workspace_size(const rast_points_t* pts, const rast_cam
     std::memset(&dummy, 0, sizeof(dummy));
     const rast_view_t v = single_view(pts, cam, &dummy, nullptr);
     Plan pl;
-    if (make_plan(&v, 1, opts, 0, pl, nullptr, true) != RAST_OK) return 0;
+    if (make_plan(&v, 1, opts, 0, pl, nullptr, kUntiledSplit) != RAST_OK) return 0;
     return pl.total;
 }
 
@@ -548,7 +655,37 @@ rast_status_t rasterize_fwd_untiled(const rast_points_t* pts, const rast_camera_
                                     void* workspace, size_t ws_bytes, const rast_images_t* out, void* stream) {
     if (!pts || !cam || !out) return RAST_ERR_ARG;
     const rast_view_t v = single_view(pts, cam, out, nullptr);
-    return run_views(&v, 1, RAST_PASS_FWD, opts, workspace, ws_bytes, stream, nullptr, true);
+    return run_views(&v, 1, RAST_PASS_FWD, opts, workspace, ws_bytes, stream, nullptr, kUntiledSplit);
+}
+
+size_t rasterize_untiled64_workspace_size(const rast_points_t* pts, const rast_camera_t* cam,
+                                          const rast_opts_t* opts) {
+    if (!pts || !cam) return 0;
+    rast_images_t dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    const rast_view_t v = single_view(pts, cam, &dummy, nullptr);
+    Plan pl;
+    if (make_plan(&v, 1, opts, 0, pl, nullptr, kUntiledKey64) != RAST_OK) return 0;
+    return pl.total;
+}
+
+int32_t rasterize_untiled64_workspace_layout(const rast_points_t* pts, const rast_camera_t* cam,
+                                             const rast_opts_t* opts, rast_ws_entry_t* out, int32_t max) {
+    if (!pts || !cam) return -1;
+    rast_images_t dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    const rast_view_t v = single_view(pts, cam, &dummy, nullptr);
+    Plan pl;
+    if (make_plan(&v, 1, opts, 0, pl, nullptr, kUntiledKey64) != RAST_OK) return -1;
+    const int r = key64_result_pair(pl);
+    return write_layout(pl, r ? S_KEYC1 : S_KEYC0, r ? S_VALC1 : S_VALC0, out, max);
+}
+
+rast_status_t rasterize_fwd_untiled64(const rast_points_t* pts, const rast_camera_t* cam, const rast_opts_t* opts,
+                                      void* workspace, size_t ws_bytes, const rast_images_t* out, void* stream) {
+    if (!pts || !cam || !out) return RAST_ERR_ARG;
+    const rast_view_t v = single_view(pts, cam, out, nullptr);
+    return run_views(&v, 1, RAST_PASS_FWD, opts, workspace, ws_bytes, stream, nullptr, kUntiledKey64);
 }
 
 rast_status_t rasterize_fwd(const rast_points_t* pts, const rast_camera_t* cam, const rast_opts_t* opts,

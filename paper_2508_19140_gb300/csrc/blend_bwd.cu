@@ -361,13 +361,49 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
 
 // ---------------------------------------------------------------- Gaussian
 
-
-__device__ __forceinline__ float warp_sum(float x) {
+// Warp sums of N values per lane by recursive halving: at each level a lane
+// keeps one half of its values and adds the partner lane's copy of that half,
+// so N values cost N/2 + N/4 + ... + 1 shuffles (plus the full butterfly over
+// the offsets left once one value remains) instead of five per value. Lane
+// (32 / N) * k returns the sum of value k. Each sum is formed over the same
+// pairing tree as an xor butterfly over offsets 16, 8, 4, 2, 1, so the bits do
+// not depend on which lane holds it or on timing.
+template <int N, int OFF>
+__device__ __forceinline__ float warp_reduce_scatter(const float (&v)[N], int lane) {
+    if constexpr (N == 1) {
+        float x = v[0];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
+        for (int o = OFF; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        return x;
+    } else {
+        float w[N / 2];
+        const bool up = (lane & OFF) != 0;
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) {
+            const float lo = v[k], hi = v[k + N / 2];
+            w[k] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, OFF);
+        }
+        return warp_reduce_scatter<N / 2, OFF / 2>(w, lane);
+    }
 }
 
+// Gaussian backward batch: records per batch and the padded contribution row.
+template <int TS>
+__host__ __device__ constexpr int gauss_bwd_batch() { return TS * TS >= 256 ? 128 : TS * TS; }
+__host__ __device__ constexpr int gauss_contrib_stride(int P) { return P | 1; }  // odd: conflict-free rows
+template <int TS, int C>
+constexpr size_t gauss_bwd_smem() {
+    return sizeof(float) * (TS * TS / 32) * gauss_bwd_batch<TS>() * gauss_contrib_stride(C + 7);
+}
+
+// Per batch of GB records: every warp (an 8x4 sub-tile) ballots the records
+// whose pixel box meets its sub-tile; for each such record that some lane
+// really blended (inside its box, m <= 9, before the pixel's last fragment)
+// the lanes compute their P contributions, sum them over the warp with one
+// reduce-scatter, and the lanes holding the sums write the record's row of the
+// warp's contribution table (rows of odd stride: conflict-free) and a hit bit.
+// After a barrier each record's loader thread adds the rows of the warps that
+// hit it, in warp order, and writes the copy's partial row.
 template <int TS, int C, bool BF16>
 __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
@@ -376,15 +412,20 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     const uint32_t* __restrict__ base, float* __restrict__ partial, uint2* __restrict__ cutoff,
     WsHeader* __restrict__ hdr) {
     constexpr int NT = TS * TS;
-    constexpr int NW = NT / 32;                   // warps = 8x4 sub-tiles
+    constexpr int NW = NT / 32;                    // warps = 8x4 sub-tiles
     constexpr int WPR = TS / 8;                    // sub-tiles per row
-    constexpr int kGBatch = NT >= 256 ? 128 : NT;  // records per backward batch
+    constexpr int GB = gauss_bwd_batch<TS>();      // records per backward batch
+    constexpr int NG = GB / 32;                    // ballot groups per batch
     constexpr int P = C + 7;  // dfeat[C], do, du, dv, dca, dcb, dcc, dz
-    __shared__ float s_um[kGBatch], s_vm[kGBatch], s_o[kGBatch], s_z[kGBatch];
-    __shared__ float s_ca[kGBatch], s_cb[kGBatch], s_cc[kGBatch];
-    __shared__ int4 s_box[kGBatch];
-    __shared__ float s_f[C][kGBatch];
-    extern __shared__ float s_contrib[];  // [NW warps][P][kGBatch]
+    constexpr int PP = P <= 8 ? 8 : (P <= 16 ? 16 : 32);
+    constexpr int LPV = 32 / PP;                   // lanes holding each warp sum
+    constexpr int PO = gauss_contrib_stride(P);
+    __shared__ float4 s_a[GB];                     // (u - 1/2, v - 1/2, opacity, depth)
+    __shared__ float4 s_c[GB];                     // conic (a, b, c), radius
+    __shared__ int4 s_box[GB];                     // pixel box (x0, x1, y0, y1)
+    __shared__ __align__(16) float s_f[GB * C];    // FP32 features
+    __shared__ uint32_t s_hit[NW * NG];            // records each warp contributed to
+    extern __shared__ float s_contrib[];           // [NW][GB][PO]
     __shared__ uint32_t s_red;
 
     const int64_t tile = order[blockIdx.x];
@@ -423,14 +464,17 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     float Sg = 0.f, SD = 0.f;
     const float Kd = -gA * Tfin;
     const uint32_t end = rg.x + maxlast;
-    const int nb = (int)((maxlast - 1) / kGBatch);
-    const bool loader = tid < kGBatch;
+    const int nb = (int)((maxlast - 1) / GB);
+    const bool loader = tid < GB;
+    const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
 
     uint4 g = make_uint4(0u, 0u, 0u, 0u), h = make_uint4(0u, 0u, 0u, 0u);
     float f[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) f[c] = 0.f;
     uint32_t gi = 0, bs = 0;
     if (loader) {
-        const uint32_t q = rg.x + (uint32_t)nb * kGBatch + tid;
+        const uint32_t q = rg.x + (uint32_t)nb * GB + tid;
         if (q < end) {
             gi = pts[q];
             const uint32_t* rp = rec + (size_t)gi * RW;
@@ -440,14 +484,14 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
             bs = base[gi];
         }
     }
-    uint32_t gi_next = (loader && nb > 0) ? pts[rg.x + (uint32_t)(nb - 1) * kGBatch + tid] : 0u;
+    uint32_t gi_next = (loader && nb > 0) ? pts[rg.x + (uint32_t)(nb - 1) * GB + tid] : 0u;
 
     for (int bi = nb; bi >= 0; --bi) {
-        const uint32_t rel0 = (uint32_t)bi * kGBatch;
+        const uint32_t rel0 = (uint32_t)bi * GB;
         const uint32_t b0 = rg.x + rel0;
-        const uint32_t bend = end < b0 + kGBatch ? end : b0 + kGBatch;
+        const uint32_t bend = end < b0 + GB ? end : b0 + GB;
         const int nrec = (int)(bend - b0);
-        for (int k = tid; k < NW * P * kGBatch; k += NT) s_contrib[k] = 0.f;
+        if (tid < NW * NG) s_hit[tid] = 0u;
         const bool have = loader && b0 + tid < bend;
         const uint32_t my_bs = bs;
         int slot = 0;
@@ -455,16 +499,10 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
             const float um = __fsub_rn(__uint_as_float(g.x), 0.5f);
             const float vm = __fsub_rn(__uint_as_float(g.y), 0.5f);
             const GaussBox bx = gauss_box(um, vm, __uint_as_float(h.w));
-            s_um[tid] = um;
-            s_vm[tid] = vm;
-            s_z[tid] = __uint_as_float(g.z);
-            s_o[tid] = __uint_as_float(g.w);
-            s_ca[tid] = __uint_as_float(h.x);
-            s_cb[tid] = __uint_as_float(h.y);
-            s_cc[tid] = __uint_as_float(h.z);
+            s_a[tid] = make_float4(um, vm, __uint_as_float(g.w), __uint_as_float(g.z));
+            s_c[tid] = make_float4(__uint_as_float(h.x), __uint_as_float(h.y), __uint_as_float(h.z), 0.f);
             s_box[tid] = make_int4(bx.x0, bx.x1, bx.y0, bx.y1);
-#pragma unroll
-            for (int c = 0; c < C; ++c) s_f[c][tid] = f[c];
+            store_row<C>(s_f + tid * C, f);
             // tile rect of the in-image box, as the projection computed it
             const int tx0 = max(bx.x0, 0) / TS, tx1 = min(bx.x1, V.W - 1) / TS;
             const int ty0 = max(bx.y0, 0) / TS;
@@ -479,10 +517,9 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
             h = *reinterpret_cast<const uint4*>(rp + 4);
             load_features<C, BF16>(rp + FW, f);
             bs = base[gi];
-            gi_next = (bi > 1) ? pts[b0 - 2 * kGBatch + tid] : 0u;
+            gi_next = (bi > 1) ? pts[b0 - 2 * GB + tid] : 0u;
         }
-        const uint32_t wmax = __reduce_max_sync(0xffffffffu, last);
-        if (wmax > rel0) {
+        if (wlast > rel0) {
 #pragma unroll 1
             for (int grp = (nrec - 1) / 32; grp >= 0; --grp) {
                 const int r0 = grp * 32;
@@ -492,37 +529,41 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
                     hit = bb.x <= sx0 + 7 && bb.y >= sx0 && bb.z <= sy0 + 3 && bb.w >= sy0;
                 }
                 uint32_t m = __ballot_sync(0xffffffffu, hit);
+                uint32_t written = 0;
                 while (m) {
                     const int bit = 31 - __clz(m);
                     m &= ~(1u << bit);
                     const int r = r0 + bit;
-                    float v[P];
-#pragma unroll
-                    for (int k = 0; k < P; ++k) v[k] = 0.f;
-                    bool act = inside && rel0 + r < last;
-                    if (act) {
-                        const int4 bb = s_box[r];
-                        act = px >= bb.x && px <= bb.y && py >= bb.z && py <= bb.w;
-                    }
+                    const int4 bb = s_box[r];
+                    bool act = inside && rel0 + r < last && px >= bb.x && px <= bb.y && py >= bb.z && py <= bb.w;
+                    float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rc = ra;
                     float dx = 0.f, dy = 0.f, mm = 0.f;
                     if (act) {
-                        dx = __fsub_rn(fpx, s_um[r]);
-                        dy = __fsub_rn(fpy, s_vm[r]);
-                        mm = gauss_m(dx, dy, s_ca[r], s_cb[r], s_cc[r]);
+                        ra = s_a[r];
+                        rc = s_c[r];
+                        dx = __fsub_rn(fpx, ra.x);
+                        dy = __fsub_rn(fpy, ra.y);
+                        mm = gauss_m(dx, dy, rc.x, rc.y, rc.z);
                         act = mm <= 9.f;
                     }
+                    if (!__any_sync(0xffffffffu, act)) continue;  // no lane blended this record
+                    written |= 1u << bit;
+                    float v[PP];
+#pragma unroll
+                    for (int k = 0; k < PP; ++k) v[k] = 0.f;
                     if (act) {
                         const float G = gauss_value(mm);
-                        const float o = s_o[r];
+                        const float o = ra.z;
                         const float og = __fmul_rn(o, G);
                         const float alpha = fminf(og, amax);
-                        const float om = __fsub_rn(1.f, alpha);
-                        const float Tk = __fdiv_rn(T, om);  // recursive: one rounding per step
-                        const float inv = __frcp_rn(om);
+                        const float inv = __frcp_rn(__fsub_rn(1.f, alpha));
+                        const float Tk = T * inv;  // T_k = T_{k+1} / (1 - alpha_k)
+                        float fr[C];
+                        load_features<C, false>(reinterpret_cast<const uint32_t*>(s_f + r * C), fr);
                         float fdot = 0.f;
 #pragma unroll
-                        for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], s_f[c][r], fdot);
-                        const float z = s_z[r];
+                        for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], fr[c], fdot);
+                        const float z = ra.w;
                         const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) * inv;
                         const float ta = Tk * alpha;
                         Sg = fmaf(ta, fdot, Sg);
@@ -532,23 +573,20 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
                         for (int c = 0; c < C; ++c) v[c] = ta * gF[c];
                         v[C + 6] = ta * gD;
                         if (og <= amax) {
-                            const float ca = s_ca[r], cbv = s_cb[r], cc = s_cc[r];
                             const float dm = -0.5f * o * G * dalpha;
                             v[C] = G * dalpha;
-                            v[C + 1] = -dm * (2.f * ca * dx + 2.f * cbv * dy);
-                            v[C + 2] = -dm * (2.f * cbv * dx + 2.f * cc * dy);
+                            v[C + 1] = -dm * (2.f * rc.x * dx + 2.f * rc.y * dy);
+                            v[C + 2] = -dm * (2.f * rc.y * dx + 2.f * rc.z * dy);
                             v[C + 3] = dm * dx * dx;
                             v[C + 4] = dm * 2.f * dx * dy;
                             v[C + 5] = dm * dy * dy;
                         }
                     }
-#pragma unroll
-                    for (int k = 0; k < P; ++k) v[k] = warp_sum(v[k]);
-                    if (lane == 0) {
-#pragma unroll
-                        for (int k = 0; k < P; ++k) s_contrib[(warp * P + k) * kGBatch + r] = v[k];
-                    }
+                    const float sum = warp_reduce_scatter<PP, 16>(v, lane);
+                    const int k = lane / LPV;
+                    if (lane % LPV == 0 && k < P) s_contrib[(warp * GB + r) * PO + k] = sum;
                 }
+                if (lane == 0) s_hit[warp * NG + grp] = written;
             }
         }
         __syncthreads();
@@ -556,13 +594,15 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
             constexpr int PS = partial_stride(P);
             float row[PS];
 #pragma unroll
-            for (int k = 0; k < PS; ++k) {
-                float acc = 0.f;
-                if (k < P) {
+            for (int k = 0; k < PS; ++k) row[k] = 0.f;
+            const int hw = tid >> 5, hb = tid & 31;
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) acc += s_contrib[(w * P + k) * kGBatch + tid];
+            for (int w = 0; w < NW; ++w) {
+                if ((s_hit[w * NG + hw] >> hb) & 1u) {
+                    const float* cp = s_contrib + (w * GB + tid) * PO;
+#pragma unroll
+                    for (int k = 0; k < P; ++k) row[k] += cp[k];
                 }
-                row[k] = acc;
             }
             store_row<PS>(partial + (size_t)(my_bs + (uint32_t)slot) * PS, row);
         }
@@ -758,28 +798,24 @@ cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts
     const unsigned grid = (unsigned)vt.tiles_total;
     if (vt.mode == 0) {
         constexpr size_t smem = bilinear_bwd_smem<TS, RPT, C, BF16>();
-        static bool set = false;
-        if (!set) {
-            cudaError_t e = cudaFuncSetAttribute(k_blend_bwd_bilinear<TS, RPT, C, BF16>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            set = true;
-        }
+        static PerDevice attr;
+        const cudaError_t e = per_device(attr, nullptr, [](int, int*) {
+            return cudaFuncSetAttribute(k_blend_bwd_bilinear<TS, RPT, C, BF16>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        });
+        if (e != cudaSuccess) return e;
         ProfScope ps("blend_bwd", s);
         k_blend_bwd_bilinear<TS, RPT, C, BF16><<<grid, TS * TS, smem, s>>>(
             vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.grow, b.cutoff, b.hdr,
             b.trace);
     } else {
-        constexpr int NT = TS * TS;
-        constexpr int GB = NT >= 256 ? 128 : NT;
-        constexpr size_t smem = sizeof(float) * (NT / 32) * (C + 7) * GB;
-        static bool set = false;
-        if (!set) {
-            cudaError_t e = cudaFuncSetAttribute(k_blend_bwd_gauss<TS, C, BF16>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            set = true;
-        }
+        constexpr size_t smem = gauss_bwd_smem<TS, C>();
+        static PerDevice attr;
+        const cudaError_t e = per_device(attr, nullptr, [](int, int*) {
+            return cudaFuncSetAttribute(k_blend_bwd_gauss<TS, C, BF16>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        });
+        if (e != cudaSuccess) return e;
         ProfScope ps("blend_bwd", s);
         k_blend_bwd_gauss<TS, C, BF16><<<grid, TS * TS, smem, s>>>(
             vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.cutoff, b.hdr);

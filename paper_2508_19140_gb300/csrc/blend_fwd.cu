@@ -291,6 +291,9 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     }
 }
 
+// Gaussian: each batch stages NT records as three 16-byte words (screen
+// position, opacity and depth; conic; pixel box) plus FP32 features, so a
+// lane reads a record with at most four broadcast shared-memory loads.
 template <int TS, int C, bool BF16>
 __global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
@@ -298,10 +301,10 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
     uint32_t* __restrict__ last_out, WsHeader* __restrict__ hdr) {
     constexpr int NT = TS * TS;
     constexpr int WPR = TS / 8;      // warps per row of 8x4 sub-tiles
-    __shared__ float s_um[NT], s_vm[NT], s_o[NT], s_z[NT];
-    __shared__ float s_ca[NT], s_cb[NT], s_cc[NT];
-    __shared__ int4 s_box[NT];
-    __shared__ float s_f[C][NT];
+    __shared__ float4 s_a[NT];       // (u - 1/2, v - 1/2, opacity, depth)
+    __shared__ float4 s_c[NT];       // conic (a, b, c), radius
+    __shared__ int4 s_box[NT];       // pixel box (x0, x1, y0, y1)
+    __shared__ __align__(16) float s_f[NT * C];
     __shared__ uint32_t s_maxstop;
 
     const int64_t tile = order[blockIdx.x];
@@ -328,6 +331,8 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
 
     uint4 g = make_uint4(0u, 0u, 0u, 0u), h = make_uint4(0u, 0u, 0u, 0u);
     float f[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) f[c] = 0.f;
     {
         const uint32_t q = rg.x + tid;
         if (q < rg.y) {
@@ -345,16 +350,10 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
             const float um = __fsub_rn(__uint_as_float(g.x), 0.5f);
             const float vm = __fsub_rn(__uint_as_float(g.y), 0.5f);
             const GaussBox bx = gauss_box(um, vm, __uint_as_float(h.w));
-            s_um[tid] = um;
-            s_vm[tid] = vm;
-            s_z[tid] = __uint_as_float(g.z);
-            s_o[tid] = __uint_as_float(g.w);
-            s_ca[tid] = __uint_as_float(h.x);
-            s_cb[tid] = __uint_as_float(h.y);
-            s_cc[tid] = __uint_as_float(h.z);
+            s_a[tid] = make_float4(um, vm, __uint_as_float(g.w), __uint_as_float(g.z));
+            s_c[tid] = make_float4(__uint_as_float(h.x), __uint_as_float(h.y), __uint_as_float(h.z), 0.f);
             s_box[tid] = make_int4(bx.x0, bx.x1, bx.y0, bx.y1);
-#pragma unroll
-            for (int c = 0; c < C; ++c) s_f[c][tid] = f[c];
+            store_row<C>(s_f + tid * C, f);
         }
         if (__syncthreads_count(!done) == 0) break;
         {
@@ -383,29 +382,30 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
                 while (m) {
                     const int r = r0 + __ffs(m) - 1;
                     m &= m - 1;
-                    if (!done) {
-                        const int4 bb = s_box[r];
-                        if (px >= bb.x && px <= bb.y && py >= bb.z && py <= bb.w) {
-                            const float dx = __fsub_rn(fpx, s_um[r]), dy = __fsub_rn(fpy, s_vm[r]);
-                            const float mm = gauss_m(dx, dy, s_ca[r], s_cb[r], s_cc[r]);
-                            if (mm <= 9.f) {
-                                const float alpha = fminf(__fmul_rn(s_o[r], gauss_value(mm)), amax);
-                                const float nT = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                                if (nT < tmin) {
-                                    done = true;
-                                    stop = rel0 + r + 1;
-                                } else {
-                                    const float ta = T * alpha;
-#pragma unroll
-                                    for (int c = 0; c < C; ++c) F[c] = fmaf(ta, s_f[c][r], F[c]);
-                                    Dp = fmaf(ta, s_z[r], Dp);
-                                    A += ta;
-                                    T = nT;
-                                    last = rel0 + r + 1;
-                                }
-                            }
-                        }
+                    if (done) continue;
+                    const int4 bb = s_box[r];
+                    if (px < bb.x || px > bb.y || py < bb.z || py > bb.w) continue;
+                    const float4 ra = s_a[r];
+                    const float4 rc = s_c[r];
+                    const float dx = __fsub_rn(fpx, ra.x), dy = __fsub_rn(fpy, ra.y);
+                    const float mm = gauss_m(dx, dy, rc.x, rc.y, rc.z);
+                    if (!(mm <= 9.f)) continue;
+                    const float alpha = fminf(__fmul_rn(ra.z, gauss_value(mm)), amax);
+                    const float nT = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                    if (nT < tmin) {
+                        done = true;
+                        stop = rel0 + r + 1;
+                        continue;
                     }
+                    float fr[C];
+                    load_features<C, false>(reinterpret_cast<const uint32_t*>(s_f + r * C), fr);
+                    const float ta = T * alpha;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) F[c] = fmaf(ta, fr[c], F[c]);
+                    Dp = fmaf(ta, ra.w, Dp);
+                    A += ta;
+                    T = nT;
+                    last = rel0 + r + 1;
                 }
                 if (__all_sync(0xffffffffu, done)) break;
             }
@@ -415,9 +415,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
 
     if (inside) {
         const int64_t pix = (int64_t)py * V.W + px;
-        float* of = V.out_feat + pix * C;
-#pragma unroll
-        for (int c = 0; c < C; ++c) of[c] = F[c];
+        store_row<C>(V.out_feat + pix * C, F);
         if (V.out_alpha) V.out_alpha[pix] = A;
         if (V.out_depth) V.out_depth[pix] = Dp;
         t_final[V.pix_off + pix] = T;
@@ -435,13 +433,12 @@ cudaError_t launch_fwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts
     const unsigned grid = (unsigned)vt.tiles_total;
     if (vt.mode == 0) {
         constexpr size_t smem = bilinear_fwd_smem<TS, RPT, C, BF16>();
-        static bool set = false;
-        if (!set) {
-            cudaError_t e = cudaFuncSetAttribute(k_blend_fwd_bilinear<TS, RPT, C, BF16>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            set = true;
-        }
+        static PerDevice attr;
+        const cudaError_t e = per_device(attr, nullptr, [](int, int*) {
+            return cudaFuncSetAttribute(k_blend_fwd_bilinear<TS, RPT, C, BF16>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        });
+        if (e != cudaSuccess) return e;
         ProfScope ps("blend_fwd", s);
         k_blend_fwd_bilinear<TS, RPT, C, BF16><<<grid, TS * TS, smem, s>>>(
             vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.hdr, b.trace);
@@ -563,6 +560,109 @@ __global__ void __launch_bounds__(256) k_blend_fwd_pixel(const ViewTable vt, con
     if ((threadIdx.x & 31) == 0 && need) atomicAdd(&hdr->needed, (unsigned long long)need);
 }
 
+// The same per-pixel lists composited by one warp per pixel (the layout of
+// the untiled rasterizer Sec. 3.2 starts from): the lanes gather 32
+// consecutive fragments' records at once and compute their alphas; the
+// transmittance then steps through the 32 alphas in list order with the
+// per-thread walk's FP32 operations (every lane runs the same serial chain on
+// shuffled alphas, so the termination decision and T_final are those of the
+// serial walk bit for bit); the chunk's F, depth and alpha sums are warp
+// reductions (tree order: within FP32 rounding of the serial sums, not bit
+// for bit).
+__device__ __forceinline__ float warp_sum_f(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+template <int C, bool BF16>
+__global__ void __launch_bounds__(256) k_blend_fwd_pixel_warp(const ViewTable vt, const uint2* __restrict__ ranges,
+                                                              const uint32_t* __restrict__ pts,
+                                                              const uint32_t* __restrict__ rec,
+                                                              float* __restrict__ t_final,
+                                                              uint32_t* __restrict__ last_out,
+                                                              WsHeader* __restrict__ hdr) {
+    constexpr int RW = RecLayout<0, C, BF16>::words;
+    constexpr int FW = RecLayout<0, C, BF16>::feat_word;
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // global pixel ("tile") id
+    const int lane = threadIdx.x & 31;
+    if (p >= vt.tiles_total) return;  // uniform per warp
+    const ViewDev& V = vt.v[view_of_tile(vt, p)];
+    const int64_t lp = p - V.tile_off;
+    const int px = (int)(lp % V.W), py = (int)(lp / V.W);
+    const uint2 rg = ranges[p];
+    const float amax = vt.alpha_max, tmin = vt.t_min;
+    float T = 1.f, A = 0.f, Dp = 0.f;
+    float F[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) F[c] = 0.f;
+    uint32_t last = 0, stop = 0;
+#pragma unroll 1
+    for (uint32_t q0 = rg.x; q0 < rg.y; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        const int nv = (int)min(32u, rg.y - q0);
+        float alpha = 0.f, z = 0.f;
+        float f[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) f[c] = 0.f;
+        if (q < rg.y) {
+            const uint32_t* rp = rec + (size_t)pts[q] * RW;
+            const uint4 g = *reinterpret_cast<const uint4*>(rp);
+            const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
+            const float o = __uint_as_float(g.w);
+            const float wx = px == bg.i0 ? __fsub_rn(1.f, bg.a) : bg.a;
+            const float wy = py == bg.j0 ? __fsub_rn(1.f, bg.b) : bg.b;
+            alpha = fminf(__fmul_rn(o, __fmul_rn(wx, wy)), amax);
+            load_features<C, BF16>(rp + FW, f);
+            z = __uint_as_float(g.z);
+        }
+        // Serial transmittance over the chunk: T_k before fragment k in lane k.
+        float Tk = 0.f;
+        int kstop = nv;
+        for (int k = 0; k < nv; ++k) {
+            const float ak = __shfl_sync(0xffffffffu, alpha, k);
+            const float nT = __fmul_rn(T, __fsub_rn(1.f, ak));
+            if (nT < tmin) {
+                kstop = k;
+                break;
+            }
+            if (lane == k) Tk = T;
+            T = nT;
+        }
+        const float ta = lane < kstop ? Tk * alpha : 0.f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) F[c] += warp_sum_f(ta * f[c]);
+        Dp += warp_sum_f(ta * z);
+        A += warp_sum_f(ta);
+        if (kstop > 0) last = q0 - rg.x + (uint32_t)kstop;
+        if (kstop < nv) {
+            stop = q0 - rg.x + (uint32_t)kstop + 1;
+            break;
+        }
+    }
+    if (lane == 0) {
+        const int64_t pix = (int64_t)py * V.W + px;
+        store_row<C>(V.out_feat + pix * C, F);
+        if (V.out_alpha) V.out_alpha[pix] = A;
+        if (V.out_depth) V.out_depth[pix] = Dp;
+        t_final[V.pix_off + pix] = T;
+        last_out[V.pix_off + pix] = last;
+        const uint32_t need = stop ? stop : rg.y - rg.x;
+        if (need) atomicAdd(&hdr->needed, (unsigned long long)need);
+    }
+}
+
+template <int C>
+cudaError_t launch_pixel_warp_c(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    const unsigned grid = (unsigned)((vt.tiles_total * 32 + 255) / 256);
+    ProfScope ps("blend_fwd_pixel_warp", s);
+    if (vt.bf16)
+        k_blend_fwd_pixel_warp<C, true><<<grid, 256, 0, s>>>(vt, b.ranges, pts, b.rec, b.t_final, b.last, b.hdr);
+    else
+        k_blend_fwd_pixel_warp<C, false><<<grid, 256, 0, s>>>(vt, b.ranges, pts, b.rec, b.t_final, b.last, b.hdr);
+    return cudaGetLastError();
+}
+
 template <int C>
 cudaError_t launch_pixel_c(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     const unsigned grid = (unsigned)((vt.tiles_total + 255) / 256);
@@ -583,6 +683,19 @@ cudaError_t launch_blend_fwd_pixel(const ViewTable& vt, const Bufs& b, const uin
         case 4: return launch_pixel_c<4>(vt, b, pts, s);
         case 8: return launch_pixel_c<8>(vt, b, pts, s);
         case 16: return launch_pixel_c<16>(vt, b, pts, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_blend_fwd_pixel_warp(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    if (vt.tiles_total == 0) return cudaSuccess;
+    switch (vt.C) {
+        case 1: return launch_pixel_warp_c<1>(vt, b, pts, s);
+        case 2: return launch_pixel_warp_c<2>(vt, b, pts, s);
+        case 3: return launch_pixel_warp_c<3>(vt, b, pts, s);
+        case 4: return launch_pixel_warp_c<4>(vt, b, pts, s);
+        case 8: return launch_pixel_warp_c<8>(vt, b, pts, s);
+        case 16: return launch_pixel_warp_c<16>(vt, b, pts, s);
         default: return cudaErrorInvalidValue;
     }
 }

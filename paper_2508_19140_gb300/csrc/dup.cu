@@ -76,18 +76,23 @@ __device__ __forceinline__ void store_rects(uint2* __restrict__ p, int64_t s0, i
 }
 
 // Sorted-order rects of a block of kScanItems points (gathered once, kept for
-// k_dup_write) and the block's copy count.
+// k_dup_write) and the block's copy count. If the depth sort failed (its
+// look-back wait ran out: the error word is set before this kernel starts),
+// every point counts as empty, so no copy is made from a partial order; an
+// index outside [0, n) is treated the same way.
 __global__ void __launch_bounds__(kT) k_dup_count(const uint32_t* __restrict__ sorted_pts,
                                                   const uint2* __restrict__ rect,
                                                   uint2* __restrict__ rectS, int64_t n,
-                                                  uint32_t* __restrict__ blk) {
+                                                  uint32_t* __restrict__ blk, const WsHeader* __restrict__ hdr) {
     __shared__ uint32_t s_warp[33];
     const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
+    const bool failed = (hdr->error & kErrTimeout) != 0u;
     uint32_t gi[kPer];
     load_u32s(sorted_pts, s0, n, gi, 0xffffffffu);
     uint2 r[kPer];
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) r[j] = gi[j] != 0xffffffffu ? rect[gi[j]] : make_uint2(1u, 0u);
+    for (int j = 0; j < kPer; ++j)
+        r[j] = (!failed && (int64_t)gi[j] < n) ? rect[gi[j]] : make_uint2(1u, 0u);
     uint32_t c = 0;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) c += rect_count(r[j]);
@@ -233,9 +238,13 @@ __global__ void __launch_bounds__(kT) k_scan_apply(const uint32_t* __restrict__ 
     }
 }
 
+// Tile ranges from the sorted tile keys. If the tile sort's look-back wait ran
+// out, the keys are a partial order: the ranges are left empty (cleared before
+// this kernel), so the blends read no copy of it.
 __global__ void __launch_bounds__(kT) k_ranges(const uint32_t* __restrict__ keys,
                                                const WsHeader* __restrict__ hdr,
                                                uint2* __restrict__ ranges) {
+    if (hdr->error & kErrTimeout) return;
     const int64_t D = hdr->n_copies;
     // Four consecutive keys per thread (one 16-byte load) plus the keys just
     // before and after them; a range starts or ends where neighbours differ.
@@ -261,18 +270,89 @@ __global__ void __launch_bounds__(kT) k_ranges(const uint32_t* __restrict__ keys
     }
 }
 
-int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
+// ---- untiled baseline with one 64-bit-key sort (the arrangement Sec. 3.2
+// "Tiled Rendering" starts from) ------------------------------------------
+// Copies in POINT order, one per in-image pixel of the point's 2x2 box (the
+// projection's rect with one-pixel tiles): the low key word is the point's
+// depth key, the high word its pixel id; the point index goes with them. A
+// stable LSD radix sort over the 64-bit key [pixel | depth] then yields the
+// per-pixel lists in (depth, point index) order, ties falling back to the
+// point order the copies were written in.
+__global__ void __launch_bounds__(kT) k_untiled_copies(const ViewTable vt, const uint2* __restrict__ rect,
+                                                       const uint32_t* __restrict__ dkey,
+                                                       const uint32_t* __restrict__ base,
+                                                       uint32_t* __restrict__ key_lo, uint32_t* __restrict__ key_hi,
+                                                       uint32_t* __restrict__ pt, int64_t cap) {
+    const int64_t gi = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (gi >= vt.n_total) return;
+    const uint2 r = rect[gi];
+    if (rect_count(r) == 0) return;
+    const ViewDev& V = vt.v[view_of_point(vt, gi)];
+    const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff, y1 = r.y >> 16;
+    const uint32_t k = dkey[gi];
+    int64_t o = base[gi];
+    for (int y = y0; y <= y1; ++y)
+        for (int x = x0; x <= x1; ++x, ++o) {
+            if (o >= cap) return;
+            key_lo[o] = k;
+            key_hi[o] = (uint32_t)(V.tile_off + (int64_t)y * V.tiles_x + x);
+            pt[o] = (uint32_t)gi;
+        }
+}
+
+// Between the low-word and high-word digit passes of the 64-bit sort: the
+// high key word and the point index of every copy, fetched by the copy id the
+// low-word passes carried (a copy id outside [0, D) yields an empty key past
+// every pixel; after a timed-out pass the count is treated as zero).
+__global__ void __launch_bounds__(kT) k_gather_hi(const uint32_t* __restrict__ cid,
+                                                  const uint32_t* __restrict__ key_hi,
+                                                  const uint32_t* __restrict__ pt,
+                                                  const WsHeader* __restrict__ hdr,
+                                                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+    if (hdr->error & kErrTimeout) return;
+    const int64_t D = hdr->n_copies;
+    for (int64_t j = (int64_t)blockIdx.x * kT + threadIdx.x; j < D; j += (int64_t)gridDim.x * kT) {
+        const uint32_t c = cid[j];
+        const bool ok = (int64_t)c < D;
+        kout[j] = ok ? key_hi[c] : 0xffffffffu;
+        vout[j] = ok ? pt[c] : 0u;
     }
-    return n;
 }
 
 }  // namespace
+
+cudaError_t launch_untiled_copies(const ViewTable& vt, const Bufs& b, const uint32_t* dkey, uint32_t* key_lo,
+                                  uint32_t* key_hi, uint32_t* pt, cudaStream_t s) {
+    const int64_t n = vt.n_total;
+    const int64_t nb = (n + kScanItems - 1) / kScanItems;
+    if (nb == 0) return cudaSuccess;
+    {
+        ProfScope ps("dup.count", s);
+        k_count_blocks<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk);
+    }
+    {
+        ProfScope ps("dup.scan", s);
+        k_scan_blocks<<<1, 1024, 0, s>>>(b.blk, nb, b.hdr, b.copy_cap);
+        k_scan_apply<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk, b.base);
+    }
+    {
+        ProfScope ps("dup.write", s);
+        k_untiled_copies<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(vt, b.rect, dkey, b.base, key_lo, key_hi, pt,
+                                                                      b.copy_cap);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_hi(const Bufs& b, const uint32_t* cid, const uint32_t* key_hi, const uint32_t* pt,
+                             uint32_t* kout, uint32_t* vout, cudaStream_t s) {
+    if (b.copy_cap == 0) return cudaSuccess;
+    int64_t g = (b.copy_cap + kT - 1) / kT;
+    const int64_t gmax = (int64_t)device_sm_count() * 16;
+    if (g > gmax) g = gmax;
+    ProfScope ps("sort64.gather_hi", s);
+    k_gather_hi<<<(unsigned)g, kT, 0, s>>>(cid, key_hi, pt, b.hdr, kout, vout);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
                              cudaStream_t s) {
@@ -281,7 +361,7 @@ cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t*
     if (nb == 0) return cudaSuccess;  // the header was zeroed at the start of the pass
     {
         ProfScope ps("dup.count", s);
-        k_dup_count<<<(unsigned)nb, kT, 0, s>>>(sorted_pts, b.rect, b.rectS, n, b.blk);
+        k_dup_count<<<(unsigned)nb, kT, 0, s>>>(sorted_pts, b.rect, b.rectS, n, b.blk, b.hdr);
     }
     {
         ProfScope ps("dup.scan", s);
@@ -300,7 +380,7 @@ cudaError_t launch_ranges(const ViewTable& vt, const Bufs& b, const uint32_t* so
     cudaError_t e = cudaMemsetAsync(b.ranges, 0, sizeof(uint2) * vt.tiles_total, s);
     if (e != cudaSuccess || b.copy_cap == 0) return e;
     int64_t g = (b.copy_cap + kT - 1) / kT;
-    const int64_t gmax = (int64_t)sm_count() * 8;
+    const int64_t gmax = (int64_t)device_sm_count() * 8;
     if (g > gmax) g = gmax;
     ProfScope ps("ranges", s);
     k_ranges<<<(unsigned)g, kT, 0, s>>>(sorted_tiles, b.hdr, b.ranges);

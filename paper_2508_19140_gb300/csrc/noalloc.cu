@@ -12,12 +12,15 @@
 // This entry point keeps those arrays in one file-scope device array of
 // kNoAllocBytes (16 MiB), which every GPU that loads the library holds until
 // the process exits. Problems whose workspace would not fit are rejected with
-// RAST_ERR_CAPACITY before any device work. All calls share the array and it
-// keeps the previous call's contents; the forward pass initialises everything
-// it reads (its header, tile ranges and sort bin totals are cleared on the
-// stream before use), so stale contents are harmless. Calls whose GPU work
-// overlaps (different streams, or different host threads, without ordering)
-// race on the array and must be serialised by the caller.
+// RAST_ERR_CAPACITY before any device work. Errors the GPU itself raises
+// during the pass (more copies than max_copies allows, a bounded wait that ran
+// out) land in the scratch's header like in a caller's workspace, and
+// rasterize_noalloc_get_status reads them back. All calls share the array and
+// it keeps the previous call's contents; the forward pass initialises
+// everything it reads (its header, tile ranges and sort bin totals are cleared
+// on the stream before use), so stale contents are harmless. Calls whose GPU
+// work overlaps (different streams, or different host threads, without
+// ordering) race on the array and must be serialised by the caller.
 #include <cstring>
 #include <mutex>
 
@@ -36,13 +39,19 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch on the current device, looked up once per
-// device (with that device current) and cached.
-rast_status_t scratch_address(void** out) {
+// Device address of the scratch on the current device (looked up with that
+// device current). Outside stream capture it is looked up on every call and
+// the cache refreshed, so a context torn down and created again (after
+// cudaDeviceReset, say) never leaves a stale address behind; while `stream`
+// is being captured the cached address is used, which is why the first call
+// on a device must come before any capture.
+rast_status_t scratch_address(cudaStream_t stream, void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RAST_ERR_CUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return RAST_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RAST_ERR_CUDA;
         g_scratch_ptr[dev] = p;
@@ -67,7 +76,17 @@ extern "C" rast_status_t rasterize_fwd_noalloc(const rast_points_t* pts, const r
     if (need == 0) return RAST_ERR_ARG;
     if (need > rast::kNoAllocBytes) return RAST_ERR_CAPACITY;  // too large for the static scratch
     void* ws = nullptr;
-    const rast_status_t st = rast::scratch_address(&ws);
+    const rast_status_t st = rast::scratch_address(static_cast<cudaStream_t>(stream), &ws);
     if (st != RAST_OK) return st;
     return rasterize_batch(&v, 1, RAST_PASS_FWD, opts, ws, rast::kNoAllocBytes, stream);
+}
+
+// Device-side status of the last rasterize_fwd_noalloc call on the current
+// device: the same header rasterize_get_status reads from a caller's
+// workspace, read here from the static scratch.
+extern "C" rast_status_t rasterize_noalloc_get_status(void* stream, rast_stats_t* stats) {
+    void* ws = nullptr;
+    const rast_status_t st = rast::scratch_address(static_cast<cudaStream_t>(stream), &ws);
+    if (st != RAST_OK) return st;
+    return rasterize_get_status(ws, rast::kNoAllocBytes, stream, stats);
 }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "inpc_rast.h"
 
 namespace rast {
@@ -57,6 +59,7 @@ struct ViewTable {
     int32_t rec_words;   // record stride in 32-bit words (multiple of 4)
     int32_t feat_word;   // first feature word in a record
     int32_t shared_tiles; // some view blends into another view's tiles (point clouds of one image)
+    int32_t flags;        // rast_opts_t::flags
     float t_min, alpha_max, dilation;
     int64_t n_total, tiles_total, pix_total;
     ViewDev v[kMaxViews];
@@ -142,6 +145,36 @@ __device__ __forceinline__ uint32_t rect_count(uint2 r) {
     return (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
 }
 
+// ---- per-device, thread-safe one-time set-up ------------------------------
+// Launch attributes (cudaFuncSetAttribute), SM counts and occupancy belong to
+// a device, not to the process: one process may drive several GPUs, from
+// several host threads. A PerDevice slot runs its set-up once per device
+// (with that device current, under std::call_once, so concurrent first calls
+// wait for one another) and keeps the result and the status of the set-up.
+constexpr int kMaxDevices = 64;
+
+struct PerDevice {
+    std::once_flag flag[kMaxDevices];
+    int value[kMaxDevices] = {};
+    cudaError_t err[kMaxDevices] = {};
+};
+
+// fn(int device, int* value) -> cudaError_t. Returns the set-up's status and
+// stores its value in *out (if non-null).
+template <typename F>
+cudaError_t per_device(PerDevice& pd, int* out, F&& fn) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(pd.flag[dev], [&] { pd.err[dev] = fn(dev, &pd.value[dev]); });
+    if (out) *out = pd.value[dev];
+    return pd.err[dev];
+}
+
+// Multiprocessor count of the current device (1 if the query fails).
+int device_sm_count();
+
 // ---- per-kernel profiling (defined in api.cu) ------------------------------
 // Opens an NVTX range named `name` for the scope (host-side, so profilers can
 // group the launches by stage; free when no profiler is attached). While
@@ -171,6 +204,8 @@ struct Bufs {
     // per copy
     uint32_t* keyC[2];
     uint32_t* valC[2];
+    uint32_t* pixC;       // untiled 64-bit-key sort: pixel id per copy (point order)
+    uint32_t* ptC;        // untiled 64-bit-key sort: point index per copy (point order)
     float* partial;       // backward per-copy partial gradients (points with several copies)
     float* grow;          // backward gradient rows of single-copy points, indexed by point
     // radix sort scratch
@@ -208,6 +243,7 @@ struct SortScratch {
     uint32_t* counters;  // [kMaxSortPasses]
     uint32_t* status;    // sort_status_words()
     uint32_t* err;       // workspace error word
+    bool stall_test = false;  // RAST_FLAG_TEST_SORT_STALL: the first pass's first tile never publishes
 };
 
 // write_vals: also write the identity point values into valA[0] (needed only
@@ -232,6 +268,15 @@ cudaError_t launch_blend_fwd(const ViewTable& vt, const Bufs& b, const uint32_t*
                              cudaStream_t s);
 // Untiled baseline: one thread per pixel walks its per-pixel fragment list.
 cudaError_t launch_blend_fwd_pixel(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s);
+// Untiled baseline with the 64-bit-key sort: copies in point order
+// (low key word: depth key, high word: pixel id, plus the point index), the
+// gather of the high word between the low-word and high-word digit passes,
+// and one warp per pixel in the blend.
+cudaError_t launch_untiled_copies(const ViewTable& vt, const Bufs& b, const uint32_t* dkey, uint32_t* key_lo,
+                                  uint32_t* key_hi, uint32_t* pt, cudaStream_t s);
+cudaError_t launch_gather_hi(const Bufs& b, const uint32_t* cid, const uint32_t* key_hi, const uint32_t* pt,
+                             uint32_t* kout, uint32_t* vout, cudaStream_t s);
+cudaError_t launch_blend_fwd_pixel_warp(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s);
 cudaError_t launch_point_scan(const ViewTable& vt, const Bufs& b, cudaStream_t s);
 cudaError_t launch_blend_bwd(const ViewTable& vt, const Bufs& b, const uint32_t* sorted_pts,
                              cudaStream_t s);

@@ -40,17 +40,6 @@ constexpr uint32_t kFlagPrefix = 2u << 30;  // inclusive prefix over tiles 0..t 
 constexpr uint32_t kValueMask = (1u << 30) - 1;
 constexpr int kLookback = 8;               // predecessor tiles read per look-back step
 
-int num_sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
-
 __device__ __forceinline__ int64_t read_count(int64_t n_host, const uint32_t* d_n) {
     return d_n ? (int64_t)(*d_n) : n_host;
 }
@@ -139,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n_host, const uint32_t* d_n, int shift,
     const uint32_t* __restrict__ ghist_pass, uint32_t* __restrict__ counter, uint32_t* __restrict__ status,
-    uint32_t* __restrict__ err) {
+    uint32_t* __restrict__ err, int stall_test) {
     constexpr int BINS = 1 << BITS;
     constexpr int VPT = BINS > kThreads ? BINS / kThreads : 1;
     extern __shared__ uint32_t smem[];
@@ -152,6 +141,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
     uint32_t* s_goff = s_gbase + BINS;             // BINS: global digit starts of the pass
     uint32_t* s_warp = s_goff + BINS;              // 33
     uint32_t* s_tile = s_warp + 33;                // 1
+    // A pass after one whose look-back wait ran out does nothing: its input
+    // is a partial order whose digit counts no longer match the histogram,
+    // so its scatter positions could leave the buffers. (Within the pass that
+    // gave up, a partial prefix only lowers positions: they stay in [0, n).)
+    if (*err & kErrTimeout) return;
     const int64_t n = read_count(n_host, d_n);
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -246,12 +240,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
             tot[q] = run;
         }
         // Publish the tile's counts, then look back for the counts of all
-        // earlier tiles and publish the inclusive prefix.
+        // earlier tiles and publish the inclusive prefix. (Test hook: with
+        // stall_test the first tile publishes nothing, so its successor's
+        // wait runs out.)
         uint32_t* my = status + tile * BINS;
+        const bool withhold = stall_test && tile == 0;
+        const uint32_t spin_limit = stall_test ? 64u : (1u << 22);
 #pragma unroll
         for (int q = 0; q < VPT; ++q) {
             const int bin = threadIdx.x * VPT + q;
-            if (bin < BINS) {
+            if (bin < BINS && !withhold) {
                 cuda::atomic_ref<uint32_t, cuda::thread_scope_device> w(my[bin]);
                 w.store((tile == 0 ? kFlagPrefix : kFlagAgg) | tot[q], cuda::memory_order_relaxed);
             }
@@ -290,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
                 if (found) break;
                 t -= j;
                 if (j < kLookback) {
-                    if (++spins > (1u << 22)) {  // a predecessor never published: give up
+                    if (++spins > spin_limit) {  // a predecessor never published: give up
                         atomicOr(err, kErrTimeout);
                         break;
                     }
@@ -352,19 +350,29 @@ cudaError_t sort_t(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32
                    const SortPlan& plan, const SortScratch& sc, cudaStream_t s, int* result_buf,
                    const char* const names[2], bool identity_vals, bool keys_out) {
     constexpr int BINS = 1 << BITS;
-    static bool attr_set = false;
+    // Launch attributes and the resident CTAs per SM of the sweep, once per
+    // device: persistent grid = as many CTAs as fit on the GPU at once (every
+    // CTA resident, so a look-back never waits on a tile no running CTA holds).
+    static PerDevice setup;
     const size_t smem = sweep_smem<BITS>();
-    if (!attr_set) {
-        cudaError_t e =
+    int per_sm = 1;
+    cudaError_t e = per_device(setup, &per_sm, [smem](int, int* v) {
+        *v = 1;
+        cudaError_t r =
             cudaFuncSetAttribute(k_sweep<BITS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_sweep<BITS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_sweep<BITS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (r != cudaSuccess) return r;
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep<BITS, false>, kThreads, smem) ==
+                cudaSuccess && occ >= 1)
+            *v = occ;
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     const int64_t tiles_cap = (cap + kSortTile - 1) / kSortTile;
-    const int sms = num_sms();
-    cudaError_t e = cudaMemsetAsync(sc.ghist, 0, sizeof(uint32_t) * plan.passes * BINS, s);
+    const int sms = device_sm_count();
+    e = cudaMemsetAsync(sc.ghist, 0, sizeof(uint32_t) * plan.passes * BINS, s);
     if (e != cudaSuccess) return e;
     {
         ProfScope ps(names[0], s);
@@ -376,15 +384,6 @@ cudaError_t sort_t(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    // Persistent grid: as many CTAs as fit on the GPU at once (every CTA
-    // resident, so a look-back never waits on a tile no running CTA holds).
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<BITS, false>, kThreads, smem) !=
-                cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-    }
     const int64_t resident = (int64_t)sms * per_sm;
     const unsigned gs = (unsigned)(tiles_cap < resident ? tiles_cap : resident);
     int cur = 0;
@@ -394,7 +393,8 @@ cudaError_t sort_t(uint32_t* keys[2], uint32_t* vals[2], int64_t n, const uint32
         uint32_t* kout = (k + 1 == plan.passes && !keys_out) ? nullptr : keys[cur ^ 1];
         kern<<<gs, kThreads, smem, s>>>(keys[cur], vals[cur], kout, vals[cur ^ 1], n, d_n,
                                                  plan.shift[k], sc.ghist + k * BINS, sc.counters + k,
-                                                 sc.status + (int64_t)k * tiles_cap * BINS, sc.err);
+                                                 sc.status + (int64_t)k * tiles_cap * BINS, sc.err,
+                                                 (k == 0 && sc.stall_test) ? 1 : 0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         cur ^= 1;

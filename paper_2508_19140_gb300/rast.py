@@ -31,6 +31,7 @@ BILINEAR, GAUSSIAN = 0, 1
 GAUSS_EWA, GAUSS_ISO = 0, 1
 F32, BF16 = 0, 1
 PASS_FWD, PASS_BWD = 1, 2
+FLAG_TEST_SORT_STALL = 1  # RAST_FLAG_TEST_SORT_STALL: failure-path tests only
 
 
 class RastError(RuntimeError):
@@ -104,6 +105,7 @@ SIGNATURES = {
     "rasterize_batch": (ct.c_int, [ct.POINTER(View), ct.c_int32, ct.c_int32, ct.POINTER(Opts),
                                    ct.c_void_p, ct.c_size_t, ct.c_void_p]),
     "rasterize_get_status": (ct.c_int, [ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.POINTER(Stats)]),
+    "rasterize_noalloc_get_status": (ct.c_int, [ct.c_void_p, ct.POINTER(Stats)]),
     "rasterize_status_string": (ct.c_char_p, [ct.c_int]),
     "rasterize_workspace_layout": (ct.c_int32, [ct.POINTER(View), ct.c_int32, ct.POINTER(Opts),
                                                 ct.POINTER(WsEntry), ct.c_int32]),
@@ -112,6 +114,11 @@ SIGNATURES = {
     "rasterize_untiled_workspace_size": (ct.c_size_t, [ct.POINTER(Points), ct.POINTER(Camera), ct.POINTER(Opts)]),
     "rasterize_fwd_untiled": (ct.c_int, [ct.POINTER(Points), ct.POINTER(Camera), ct.POINTER(Opts), ct.c_void_p,
                                          ct.c_size_t, ct.POINTER(Images), ct.c_void_p]),
+    "rasterize_untiled64_workspace_size": (ct.c_size_t, [ct.POINTER(Points), ct.POINTER(Camera), ct.POINTER(Opts)]),
+    "rasterize_untiled64_workspace_layout": (ct.c_int32, [ct.POINTER(Points), ct.POINTER(Camera), ct.POINTER(Opts),
+                                                          ct.POINTER(WsEntry), ct.c_int32]),
+    "rasterize_fwd_untiled64": (ct.c_int, [ct.POINTER(Points), ct.POINTER(Camera), ct.POINTER(Opts), ct.c_void_p,
+                                           ct.c_size_t, ct.POINTER(Images), ct.c_void_p]),
     "rasterize_clouds_workspace_size": (ct.c_size_t, [ct.POINTER(Points), ct.c_int32, ct.POINTER(Camera),
                                                       ct.POINTER(Opts)]),
     "rasterize_clouds": (ct.c_int, [ct.POINTER(Points), ct.POINTER(Grads), ct.c_int32, ct.POINTER(Camera),
@@ -169,7 +176,7 @@ def _check(status, what):
 # ---------------------------------------------------------------- marshalling
 
 def make_opts(mode="bilinear", gauss_cov="ewa", tile=16, blend_depth=0, t_min=1e-4,
-              alpha_max=0.99, dilation=0.16, max_copies=0) -> Opts:
+              alpha_max=0.99, dilation=0.16, max_copies=0, flags=0) -> Opts:
     o = Opts()
     load_library().rast_default_opts(ct.byref(o))
     o.mode = {"bilinear": BILINEAR, "gaussian": GAUSSIAN}.get(mode, mode)
@@ -177,6 +184,7 @@ def make_opts(mode="bilinear", gauss_cov="ewa", tile=16, blend_depth=0, t_min=1e
     o.tile, o.blend_depth = int(tile), int(blend_depth)
     o.t_min, o.alpha_max, o.dilation = float(t_min), float(alpha_max), float(dilation)
     o.max_copies = int(max_copies)
+    o.flags = int(flags)
     return o
 
 
@@ -272,10 +280,19 @@ def rasterize_fwd(points: Points, camera: Camera, opts: Opts, workspace, out: Im
 def rasterize_fwd_noalloc(points: Points, camera: Camera, opts: Opts, out: Images, stream=None):
     """Forward of one view without a workspace or any device allocation (the
     library's static 16 MiB scratch holds the intermediates); raises RastError
-    with RAST_ERR_CAPACITY when the problem does not fit."""
+    with RAST_ERR_CAPACITY when the problem does not fit. Errors the GPU
+    raises during the pass are read with rasterize_noalloc_get_status."""
     s = load_library().rasterize_fwd_noalloc(ct.byref(points), ct.byref(camera), ct.byref(opts),
                                              ct.byref(out), _stream(stream))
     _check(s, "rasterize_fwd_noalloc")
+
+
+def rasterize_noalloc_get_status(stream=None):
+    """(status, counters) of the last rasterize_fwd_noalloc on this device."""
+    st = Stats()
+    s = load_library().rasterize_noalloc_get_status(_stream(stream), ct.byref(st))
+    stats = {f: getattr(st, f) for f, _ in Stats._fields_}
+    return int(s), stats
 
 
 def rasterize_bwd(points: Points, camera: Camera, opts: Opts, workspace, grads: Grads, stream=None):
@@ -334,6 +351,29 @@ def rasterize_fwd_untiled(points: Points, camera: Camera, opts: Opts, workspace,
                                                 _ptr(workspace), _nbytes(workspace),
                                                 ct.byref(out), _stream(stream)),
            "rasterize_fwd_untiled")
+
+
+def rasterize_untiled64_workspace_size(points: Points, camera: Camera, opts: Opts) -> int:
+    n = load_library().rasterize_untiled64_workspace_size(ct.byref(points), ct.byref(camera), ct.byref(opts))
+    if n == 0:
+        raise RastError(RAST_ERR_ARG, "rasterize_untiled64_workspace_size")
+    return int(n)
+
+
+def rasterize_untiled64_workspace_layout(points: Points, camera: Camera, opts: Opts) -> dict:
+    L = load_library()
+    n = L.rasterize_untiled64_workspace_layout(ct.byref(points), ct.byref(camera), ct.byref(opts), None, 0)
+    if n < 0:
+        raise RastError(RAST_ERR_ARG, "rasterize_untiled64_workspace_layout")
+    ents = (WsEntry * n)()
+    L.rasterize_untiled64_workspace_layout(ct.byref(points), ct.byref(camera), ct.byref(opts), ents, n)
+    return {e.name.decode(): (int(e.offset), int(e.bytes)) for e in ents}
+
+
+def rasterize_fwd_untiled64(points: Points, camera: Camera, opts: Opts, workspace, out: Images, stream=None):
+    s = load_library().rasterize_fwd_untiled64(ct.byref(points), ct.byref(camera), ct.byref(opts),
+                                               _ptr(workspace), _nbytes(workspace), ct.byref(out), _stream(stream))
+    _check(s, "rasterize_fwd_untiled64")
 
 
 def rasterize_clouds_workspace_size(clouds, camera: Camera, opts: Opts) -> int:

@@ -16,7 +16,7 @@ class Run:
     """Forward (and optionally backward) of one or several views."""
 
     def __init__(self, views, mode="bilinear", bf16=False, gauss_cov="ewa", backward=False,
-                 g_alpha=True, g_depth=True, **opt_kw):
+                 g_alpha=True, g_depth=True, ws_fill=0, **opt_kw):
         self.views = views
         self.opts = rast.make_opts(mode=mode, gauss_cov=gauss_cov, **opt_kw)
         self.gauss = mode == "gaussian"
@@ -52,7 +52,9 @@ class Run:
             cviews.append(cv)
         self.cviews = cviews
         self.ws_bytes = rast.rasterize_workspace_size(cviews, self.opts)
-        self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=DEV)
+        # ws_fill: byte the workspace holds before the first call (0xFF checks
+        # that no kernel reads anything it did not write in this call).
+        self.ws = torch.full((self.ws_bytes,), ws_fill, dtype=torch.uint8, device=DEV)
         self.layout = rast.rasterize_workspace_layout(cviews, self.opts)
         rast.rasterize_batch(cviews, rast.PASS_FWD, self.opts, self.ws)
         self.status, self.stats = rast.rasterize_get_status(self.ws)

@@ -1,9 +1,12 @@
-"""GPU parity at the benchmark's full sizes, in the launch configuration
-bench.py times: the whole sorted copy list exactly, and per-pixel /
-per-point outputs on samples the oracle computes one by one.
+"""GPU parity at the benchmark's full sizes: the whole sorted copy list
+exactly, and per-pixel / per-point outputs on samples the oracle computes one
+by one.
 
 Workload: 4,194,304 clustered points, 1280x832, bilinear, 4 FP32 features,
-fwd + bwd (the training-shape frame bench.py measures)."""
+fwd + bwd (the training-shape frame bench.py measures), at two work splits:
+the default 16x16 tiles with one record per thread per batch, and 8x8 tiles
+with blend depth 64, the split the autotuner picks for this frame and the
+one bench.py times."""
 import numpy as np
 import pytest
 import torch
@@ -15,24 +18,30 @@ from gpu_util import Run
 
 pytestmark = pytest.mark.gpu
 
-KW = dict(mode="bilinear", tile=16, pin32=True)
+SPLITS = [(16, 256), (8, 64)]  # (tile edge, blend depth)
 
 
 @pytest.fixture(scope="module")
-def frame():
+def scene_view():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2508_19140_gb300 import build
     build.build()
     oracle.build()
-    scene = scenes.make_scene(2)
-    v = scene.views[0]
-    r = Run([v], backward=True)
-    return v, r
+    return scenes.make_scene(2).views[0]
+
+
+@pytest.fixture(scope="module", params=SPLITS, ids=lambda p: f"tile{p[0]}_depth{p[1]}")
+def frame(request, scene_view):
+    tile, depth = request.param
+    r = Run([scene_view], backward=True, tile=tile, blend_depth=depth)
+    yield scene_view, r, dict(mode="bilinear", tile=tile, pin32=True)
+    del r
+    torch.cuda.empty_cache()
 
 
 def test_depth_sort_is_sorted_permutation(frame):
-    v, r = frame
+    v, r, KW = frame
     n = len(v.xyz)
     vals = r.arr("depth_sorted", np.uint32, n)
     assert np.array_equal(np.sort(vals), np.arange(n, dtype=np.uint32))
@@ -50,7 +59,7 @@ def test_depth_sort_is_sorted_permutation(frame):
 
 
 def test_full_copy_list_exact(frame):
-    v, r = frame
+    v, r, KW = frame
     tiles, idx = oracle.tile_lists(v.xyz, v.camera, **KW)
     keys, vals = r.sorted_copies()
     assert int(r.stats["n_copies"]) == len(tiles)
@@ -59,7 +68,7 @@ def test_full_copy_list_exact(frame):
 
 
 def test_sampled_pixels(frame):
-    v, r = frame
+    v, r, KW = frame
     W, H = v.camera.width, v.camera.height
     rng = np.random.default_rng(0)
     pix = rng.choice(W * H, 3000, replace=False)
@@ -73,13 +82,13 @@ def test_sampled_pixels(frame):
 
 
 def test_needed_records(frame):
-    v, r = frame
+    v, r, KW = frame
     ref = oracle.render(v.xyz, v.opacity, v.feat, v.camera, **KW)
     assert int(r.stats["needed_records"]) == ref["needed"]
 
 
 def test_sampled_point_gradients(frame):
-    v, r = frame
+    v, r, KW = frame
     rng = np.random.default_rng(1)
     pm = np.zeros(len(v.xyz), np.uint8)
     pm[rng.choice(len(v.xyz), 2000, replace=False)] = 1
@@ -96,7 +105,7 @@ def test_sampled_point_gradients(frame):
 def test_rerun_bit_identical(frame):
     """Two more fwd+bwd runs on the same workspace reproduce every output bit
     (no order-dependent shared-memory or atomic effects at full size)."""
-    v, r = frame
+    v, r, KW = frame
     from paper_2508_19140_gb300 import rast
     F0, A0, D0 = (x.copy() for x in r.image())
     tf0, last0 = (x.copy() for x in r.pixel_state())

@@ -40,9 +40,8 @@ def _check_view(r, k, v, kw, feat, pix_n=1500, pts_n=400, backward=True, seed=0)
     ok = ref["margin"] > 1e-5 if kw["mode"] == "gaussian" else np.ones(len(pix), bool)
     assert ok.mean() > 0.98
     F, A, D = r.image(k)
-    rt = 2e-5 if kw["mode"] == "gaussian" else 1e-5
-    np.testing.assert_allclose(F.reshape(-1, F.shape[-1])[pix][ok], ref["F"][ok], rtol=rt, atol=1e-7)
-    np.testing.assert_allclose(A.reshape(-1)[pix][ok], ref["alpha"][ok], rtol=rt, atol=1e-7)
+    np.testing.assert_allclose(F.reshape(-1, F.shape[-1])[pix][ok], ref["F"][ok], rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(A.reshape(-1)[pix][ok], ref["alpha"][ok], rtol=1e-5, atol=1e-7)
     _, last = r.pixel_state(k)
     assert np.array_equal(last.reshape(-1)[pix][ok], ref["last_pos"][ok].astype(np.uint32))
     if not backward:

@@ -147,9 +147,11 @@ def test_forward_gaussian(name, cov):
     ref = oracle.render(v.xyz, v.opacity, v.feat, v.camera, scale=v.scale, **oracle_kw("gaussian", cov))
     # exp() may differ by an ulp between the CPU and GPU libraries: pixels whose
     # termination decision sits within that of the threshold are not comparable.
+    # Every other pixel is held to the FP32 image bar (measured: at most
+    # 6e-7 relative on these cases).
     ok = ref["margin"] > 1e-5
     assert ok.mean() > 0.99
-    _check_image(r, ref, ok, rtol=2e-5)
+    _check_image(r, ref, ok)
     tf, last = r.pixel_state()
     assert np.array_equal(last[ok], ref["last_pos"][ok].astype(np.uint32))
 
@@ -215,9 +217,14 @@ def test_bf16_features_forward_and_backward():
     # Total error against FP32 features: BF16 rounds each (non-negative) feature
     # by at most its unit roundoff 2^-8 relative, and the blend weights are
     # non-negative, so |F_bf16 - F| <= 2^-8 F plus the accumulation error.
+    # Elementwise, 2e-3 relative is below BF16's own unit roundoff (2^-8 =
+    # 3.9e-3): a pixel dominated by one fragment carries that fragment's
+    # rounding whole. Normwise over the image, where roundings of many
+    # features average out, 2e-3 holds.
     ref_f = oracle.render(v.xyz, v.opacity, v.feat, v.camera, **oracle_kw("bilinear"))
     F, _, _ = r.image()
     assert np.all(np.abs(F - ref_f["F"]) <= (2.0 ** -8 + 2e-5) * np.abs(ref_f["F"]) + 1e-6)
+    assert np.linalg.norm(F - ref_f["F"]) / np.linalg.norm(ref_f["F"]) <= 2e-3
     g = r.grads()
     ref = oracle.backward(v.xyz, v.opacity, fb, v.camera, v.g_feat, v.g_alpha, v.g_depth,
                           **oracle_kw("bilinear"))
@@ -260,6 +267,30 @@ def test_deterministic_rerun(name, bf16):
             assert np.array_equal(x, y)
         for key, val in runs[0].grads().items():
             assert np.array_equal(val, r.grads()[key]), key
+
+
+# ----------------------------------------------------------------------------- stale workspace
+
+@pytest.mark.parametrize("name,tile,depth", [("tiny", 16, 0), ("dense", 8, 64), ("ragged", 8, 64),
+                                             ("gauss", 16, 0), ("gauss", 8, 0)])
+def test_workspace_prefilled_with_ones_gives_same_bits(name, tile, depth):
+    """Every workspace array a kernel reads is written earlier in the same
+    call: a workspace whose bytes are all 0xFF before the call gives the same
+    images, per-pixel state, copy lists and gradients, bit for bit, as a
+    zeroed one."""
+    v = case_view(name)
+    mode = _mode(name)
+    a = Run([v], mode=mode, backward=True, tile=tile, blend_depth=depth)
+    b = Run([v], mode=mode, backward=True, tile=tile, blend_depth=depth, ws_fill=0xFF)
+    assert a.status == 0 and b.status == 0
+    for x, y in zip(a.image(), b.image()):
+        assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+    for x, y in zip(a.pixel_state(), b.pixel_state()):
+        assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+    for x, y in zip(a.sorted_copies(), b.sorted_copies()):
+        assert np.array_equal(x, y)
+    for key, val in a.grads().items():
+        assert np.array_equal(val.view(np.uint32), b.grads()[key].view(np.uint32)), key
 
 
 # ----------------------------------------------------------------------------- edge cases
@@ -358,6 +389,27 @@ def test_capacity_overflow_is_reported_not_written():
     assert st == 2  # RAST_ERR_CAPACITY
     F, A, _ = r.image()  # nothing is blended from a truncated list
     assert np.all(F == 0) and np.all(A == 0)
+
+
+def test_bounded_wait_runs_out_and_is_reported():
+    """Failure detection without a fault: the test hook makes the depth
+    sort's first pass withhold one look-back word, so the next tile's bounded
+    wait runs out. The call must return, report RAST_ERR_TIMEOUT, blend
+    nothing from the partial order (empty images, zero gradients), and leave
+    the context usable: a normal call right after matches the oracle."""
+    from paper_2508_19140_gb300 import rast
+    v = scenes.random_small_view(31, 20000, 96, 64)  # > 4096 points: several sort tiles
+    r = Run([v], backward=True, flags=rast.FLAG_TEST_SORT_STALL, ws_fill=0xFF)
+    assert r.status == rast.RAST_ERR_TIMEOUT
+    assert r.stats["n_copies"] == 0
+    F, A, D = r.image()
+    assert np.all(F == 0) and np.all(A == 0) and np.all(D == 0)
+    for key, val in r.grads().items():
+        assert np.all(val == 0), key
+    ok = Run([v], backward=True)
+    assert ok.status == 0
+    ref = oracle.render(v.xyz, v.opacity, v.feat, v.camera, **oracle_kw("bilinear"))
+    _check_image(ok, ref)
 
 
 def test_wide_depth_range_uses_widest_digits():
