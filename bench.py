@@ -619,10 +619,13 @@ def run_contract(tens, dev, stream, flush, peak, reps):
 
 
 def run_untiled(scene, tens, dev, stream, flush, reps):
-    """Forward of the same frame with the untiled baseline (per-pixel lists,
-    ~4 copies per point, one thread per pixel) against the tiled forward at
-    16x16 and 8x8 tiles, with the per-kernel split of the untiled run: what
-    tiling saves on this GPU (Sec. 3.2 "Tiled Rendering")."""
+    """Forward of the same frame with the two untiled baselines (per-pixel
+    lists, ~4 copies per point): through the split sort with one thread per
+    pixel, and through one 64-bit [pixel | depth] key sort with one warp per
+    pixel (the arrangement the paper's 28n sort cost refers to), against the
+    tiled forward at 16x16 and 8x8 tiles, with the per-kernel split of the
+    untiled runs: what tiling and the split sort save on this GPU (Sec. 3.2
+    "Tiled Rendering")."""
     import torch
 
     from paper_2508_19140_gb300 import rast
@@ -658,6 +661,20 @@ def run_untiled(scene, tens, dev, stream, flush, reps):
     rast.rasterize_profile_enable(False)
     res["untiled_kernels_ms"] = {k: round(b, 4) for k, (a, b) in prof.items()}
     res["untiled_copies"] = int(rast.rasterize_get_status(ws_u, stream)[1]["n_copies"])
+    # The same per-pixel lists from ONE 64-bit [pixel | depth] key sort of the
+    # copies (7 digit passes over ~4n copies: the paper's 28n), one warp per pixel.
+    ws_k = torch.empty(rast.rasterize_untiled64_workspace_size(pts, cam, o_u), dtype=torch.uint8, device=dev)
+    res["untiled64_fwd_ms"] = round(timed(lambda: rast.rasterize_fwd_untiled64(pts, cam, o_u, ws_k, out, stream)), 4)
+    rast.rasterize_profile_enable(True)
+    rast.rasterize_fwd_untiled64(pts, cam, o_u, ws_k, out, stream)
+    prof = rast.rasterize_profile_read()
+    rast.rasterize_profile_enable(False)
+    res["untiled64_kernels_ms"] = {k: round(b, 4) for k, (a, b) in prof.items()}
+    res["untiled64_sort_passes"] = {k: int(a) for k, (a, b) in prof.items() if k.endswith(".sweep")}
+    res["untiled64_sort_ms"] = round(sum(b for k, (a, b) in prof.items() if k.startswith("sort64")), 4)
+    res["split_untiled_sort_ms"] = round(sum(b for k, b in res["untiled_kernels_ms"].items()
+                                             if k.startswith(("depth_sort", "tile_sort"))), 4)
+    del ws_k
     for tile in (16, 8):
         o_t = rast.make_opts(mode="bilinear", tile=tile)
         ws_t = torch.empty(rast.rasterize_workspace_size([_single(pts, cam, out)], o_t), dtype=torch.uint8,
@@ -666,6 +683,7 @@ def run_untiled(scene, tens, dev, stream, flush, reps):
         if tile == 16:
             res["tiled16_copies"] = int(rast.rasterize_get_status(ws_t, stream)[1]["n_copies"])
     res["speedup_tiled16_vs_untiled"] = round(res["untiled_fwd_ms"] / res["tiled16_fwd_ms"], 3)
+    res["speedup_tiled16_vs_untiled64"] = round(res["untiled64_fwd_ms"] / res["tiled16_fwd_ms"], 3)
     return res
 
 
