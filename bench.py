@@ -279,7 +279,10 @@ def run_ours(args, ws_, rank, local):
                               scale_points=args.scale_points)
     bf16 = scene.feat_dtype == "bf16"
     gauss = scene.mode == "gaussian"
-    opts = rast.make_opts(mode=scene.mode, tile=args.tile or 16, blend_depth=args.blend_depth)
+    # Training workloads keep the forward's tile-ordered record copy for the
+    # backward (RAST_FLAG_SAVE_FOR_BWD); inference workloads do not need it.
+    flags = rast.FLAG_SAVE_FOR_BWD if scene.backward else 0
+    opts = rast.make_opts(mode=scene.mode, tile=args.tile or 16, blend_depth=args.blend_depth, flags=flags)
     tens, cviews = make_views(scene, dev, bf16)
     tune = None
     if args.tile == 0:
@@ -288,10 +291,11 @@ def run_ours(args, ws_, rank, local):
         from paper_2508_19140_gb300 import autotune
         tr = autotune.autotune(cviews, opts, rast.PASS_FWD | (rast.PASS_BWD if scene.backward else 0),
                                torch.cuda.current_stream(dev))
-        opts = autotune.with_split(opts, tr.tile, tr.blend_depth)
-        tune = {"tile": tr.tile, "blend_depth": tr.blend_depth, "from_cache": tr.from_cache,
-                "timings_ms": {f"{t}x{d}": (round(ms, 4) if ms is not None else None)
-                               for (t, d), ms in tr.timings_ms.items()}}
+        opts = autotune.with_split(opts, tr.tile, tr.blend_depth, tr.save_copy)
+        tune = {"tile": tr.tile, "blend_depth": tr.blend_depth, "record_copy": tr.save_copy,
+                "from_cache": tr.from_cache,
+                "timings_ms": {autotune._label(c): (round(ms, 4) if ms is not None else None)
+                               for c, ms in tr.timings_ms.items()}}
     ws_bytes = rast.rasterize_workspace_size(cviews, opts)
     wsp = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -372,7 +376,8 @@ def run_ours(args, ws_, rank, local):
 
     seq = None
     if len(scene.views) > 1 and bf16 and rank == 0:
-        seq_ms = sequential_f32_ms(scene, dev, rast.make_opts(mode=scene.mode), max(3, args.steps // 4), flush)
+        seq_ms = sequential_f32_ms(scene, dev, rast.make_opts(mode=scene.mode, flags=flags),
+                                   max(3, args.steps // 4), flush)
         seq = {"sequential_f32_ms": round(seq_ms, 4),
                "batched_bf16_graph_ms": round(total_ms / max(args.steps, 1), 4),
                "speedup": round(seq_ms / (total_ms / max(args.steps, 1)), 3),

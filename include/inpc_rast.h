@@ -92,8 +92,18 @@ typedef struct {
     float alpha_max;       /* alpha clamp (0.99) */
     float dilation;        /* screen-space dilation variance, Gaussian mode (0.16) */
     int32_t max_copies;    /* capacity: point-tile copies per point (0 = 4 bilinear, 16 Gaussian) */
-    int32_t flags;         /* 0, or RAST_FLAG_TEST_SORT_STALL (testing the failure path only) */
+    int32_t flags;         /* 0 or an OR of RAST_FLAG_SAVE_FOR_BWD and RAST_FLAG_TEST_SORT_STALL */
 } rast_opts_t;
+
+/* The forward blend also writes a copy of every point record it reads, in
+ * tile-list order, into the workspace (bilinear mode, tiled calls; the
+ * workspace grows by one record per copy of the capacity), so that a backward
+ * pass on the same workspace reads its records as sequential runs instead of
+ * gathering them by point index. Results are identical either way; a backward
+ * after a forward without the flag gathers. Set it when a backward will
+ * follow (training), leave it out for inference. Pass the same flags to
+ * rasterize_workspace_size and to every call on that workspace. */
+#define RAST_FLAG_SAVE_FOR_BWD 2
 
 /* Test hook for the bounded device-side waits (failure detection). With this
  * flag the first digit pass of the depth sort withholds the look-back word of

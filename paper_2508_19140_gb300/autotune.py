@@ -1,4 +1,6 @@
-"""Autotuner for the rasterizer's work split: tile edge and blend depth.
+"""Autotuner for the rasterizer's work split: tile edge, blend depth and,
+for training steps, whether the forward keeps a tile-ordered copy of the
+records for the backward.
 
 The paper renders with 16x16 tiles (Sec. 3.2, "Tiled Rendering"); the tile
 edge and the number of records staged per blend batch change only how the
@@ -10,7 +12,12 @@ critical path in dense regions) but create more point-tile copies to sort and
 reduce. So the choice is measured, not guessed:
 
   * the candidates are the compiled (tile, depth) pairs the library reports
-    (``rasterize_tune_candidates``), default first;
+    (``rasterize_tune_candidates``), default first; when the caller runs a
+    bilinear backward on the workspace and allows the record copy
+    (RAST_FLAG_SAVE_FOR_BWD in its opts), each pair is also tried with the
+    copy, after every pair without it (the copy costs the forward one
+    sequential write per record and saves the backward its random gathers:
+    it pays off once the records no longer fit in L2);
   * each is timed on the caller's own views for the caller's passes (whole
     step: projection, both sorts, blend, and the backward when asked), with
     CUDA events on the caller's stream after warm-up, L2 flushed between
@@ -69,7 +76,7 @@ def tune_key(device_name: str, opts, cviews, passes: int) -> str:
 
 
 def select(timings: dict, margin: float = 0.01) -> tuple:
-    """Fastest (tile, depth), where a later candidate must beat the best
+    """Fastest candidate, where a later candidate must beat the best
     earlier one by more than `margin` (relative): near-ties, which run-to-run
     noise would otherwise decide, go to the earlier candidate (the default
     first), so the choice is stable."""
@@ -87,6 +94,22 @@ class TuneResult:
     timings_ms: dict = field(default_factory=dict)
     key: str = ""
     from_cache: bool = False
+    save_copy: bool = False  # RAST_FLAG_SAVE_FOR_BWD in the chosen opts
+
+
+def _label(cand) -> str:
+    t, d, save = cand
+    return f"{t}x{d}" + ("+copy" if save else "")
+
+
+def candidates_for(opts, passes: int, pairs) -> list:
+    """(tile, depth, save_copy) triples to time: every pair as the caller's
+    flag has it, and, when the copy can matter (bilinear, a backward, the
+    caller allows it), every pair again with the copy."""
+    allow = bool(int(opts.flags) & rast.FLAG_SAVE_FOR_BWD)
+    if allow and (passes & rast.PASS_BWD) and int(opts.mode) == rast.BILINEAR:
+        return [(t, d, False) for t, d in pairs] + [(t, d, True) for t, d in pairs]
+    return [(t, d, allow) for t, d in pairs]
 
 
 def load_cache(path: str | None = None) -> dict:
@@ -103,8 +126,8 @@ def store_cache(key: str, res: TuneResult, path: str | None = None):
     path = path or cache_path()
     os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
     d = load_cache(path)
-    d[key] = {"tile": res.tile, "blend_depth": res.blend_depth,
-              "timings_ms": {f"{t}x{dp}": ms for (t, dp), ms in res.timings_ms.items()},
+    d[key] = {"tile": res.tile, "blend_depth": res.blend_depth, "save_copy": bool(res.save_copy),
+              "timings_ms": {_label(c): ms for c, ms in res.timings_ms.items()},
               "time": time.strftime("%Y-%m-%dT%H:%M:%S")}
     fd, tmp = tempfile.mkstemp(prefix=".autotune.", dir=os.path.dirname(path) or ".")
     with os.fdopen(fd, "w") as f:
@@ -112,10 +135,14 @@ def store_cache(key: str, res: TuneResult, path: str | None = None):
     os.replace(tmp, path)
 
 
-def with_split(opts, tile: int, depth: int):
+def with_split(opts, tile: int, depth: int, save_copy: bool | None = None):
+    """A copy of `opts` with this split (and the record-copy flag set or
+    cleared, unless save_copy is None)."""
     o = rast.Opts()
     ct.memmove(ct.byref(o), ct.byref(opts), ct.sizeof(rast.Opts))
     o.tile, o.blend_depth = int(tile), int(depth)
+    if save_copy is not None:
+        o.flags = (int(o.flags) | rast.FLAG_SAVE_FOR_BWD) if save_copy else (int(o.flags) & ~rast.FLAG_SAVE_FOR_BWD)
     return o
 
 
@@ -155,28 +182,30 @@ def cuda_timer(cviews, passes: int, stream=None, reps: int = 5, warmup: int = 2)
 def autotune(cviews, opts, passes: int = rast.PASS_FWD | rast.PASS_BWD, stream=None, *,
              device_name: str | None = None, timer=None, use_cache: bool = True,
              cache_file: str | None = None, candidates=None) -> TuneResult:
-    """Pick (tile, blend_depth) for these views; returns the result and leaves
-    ``opts`` untouched (apply it with ``with_split``)."""
+    """Pick (tile, blend_depth, record copy) for these views; returns the
+    result and leaves ``opts`` untouched (apply it with ``with_split``)."""
     if device_name is None:
         import torch
         device_name = torch.cuda.get_device_name()
+    allow = bool(int(opts.flags) & rast.FLAG_SAVE_FOR_BWD)
     key = tune_key(device_name, opts, cviews, passes)
     if use_cache:
         hit = load_cache(cache_file).get(key)
         if hit and "tile" in hit and "blend_depth" in hit:
-            return TuneResult(int(hit["tile"]), int(hit["blend_depth"]), {}, key, True)
+            return TuneResult(int(hit["tile"]), int(hit["blend_depth"]), {}, key, True,
+                              bool(hit.get("save_copy", False)) and allow)
     if candidates is None:
-        mode = int(opts.mode)
-        candidates = rast.rasterize_tune_candidates(mode)
+        candidates = rast.rasterize_tune_candidates(int(opts.mode))
+    cands = candidates_for(opts, passes, [c[:2] for c in candidates])
     if timer is None:
         timer = cuda_timer(cviews, passes, stream)
     timings = {}
-    for tile, depth in candidates:
-        timings[(tile, depth)] = timer(with_split(opts, tile, depth))
+    for c in cands:
+        timings[c] = timer(with_split(opts, c[0], c[1], c[2]))
     best = select(timings)
     if best is None:
         raise RuntimeError(f"autotune: no candidate ran ({timings})")
-    res = TuneResult(best[0], best[1], timings, key, False)
+    res = TuneResult(best[0], best[1], timings, key, False, bool(best[2]))
     if use_cache:
         store_cache(key, res, cache_file)
     return res

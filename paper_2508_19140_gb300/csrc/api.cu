@@ -40,13 +40,13 @@ int bit_length(uint64_t x) {
 enum Slot {
     S_HDR, S_REC, S_RECT, S_CNT, S_ZBITS, S_KEYA0, S_KEYA1, S_VALA0, S_VALA1, S_RECTS, S_BASE, S_BLK,
     S_KEYC0, S_KEYC1, S_VALC0, S_VALC1, S_PARTIAL, S_GROW, S_SGHIST, S_SCOUNT, S_SSTATUS, S_RANGES, S_ORDER, S_CUTOFF, S_TRACE,
-    S_TFINAL, S_LAST, S_PIXC, S_PTC, S_COUNT
+    S_TFINAL, S_LAST, S_PIXC, S_PTC, S_RECTILE, S_COUNT
 };
 const char* kSlotNames[S_COUNT] = {
     "header", "records", "rect", "count", "zbits", "keys_a0", "keys_a1", "vals_a0", "vals_a1",
     "rect_sorted", "base", "block_sums", "keys_c0", "keys_c1", "vals_c0", "vals_c1",
     "partial", "grad_rows", "sort_hist", "sort_counters", "sort_status", "ranges", "tile_order", "cutoff", "tile_trace", "t_final", "last",
-    "copy_pixel", "copy_point"};
+    "copy_pixel", "copy_point", "records_tiled"};
 
 // Arrangements of the pipeline.
 enum Arrangement {
@@ -64,6 +64,7 @@ struct Plan {
     SortPlan planA, planC;
     int partial_floats;
     int arrangement;
+    bool save_tiled;  // the forward writes the tile-ordered record copy
 };
 
 int32_t write_layout(const Plan& pl, int keys_slot, int vals_slot, rast_ws_entry_t* out, int32_t max);
@@ -110,7 +111,7 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     if (!untiled && !blend_depth_supported(o->mode, o->tile, depth)) return RAST_ERR_NOT_SUPPORTED;
     if (!(o->t_min >= 0.f) || !(o->alpha_max > 0.f && o->alpha_max < 1.f)) return RAST_ERR_ARG;
     if (!(o->dilation >= 0.f) || o->max_copies < 0) return RAST_ERR_ARG;
-    if ((o->flags & ~RAST_FLAG_TEST_SORT_STALL) != 0) return RAST_ERR_ARG;
+    if ((o->flags & ~(RAST_FLAG_TEST_SORT_STALL | RAST_FLAG_SAVE_FOR_BWD)) != 0) return RAST_ERR_ARG;
     const int C = views[0].pts.channels;
     const int dt = views[0].pts.feat_dtype;
     if (dt != RAST_F32 && dt != RAST_BF16) return RAST_ERR_ARG;
@@ -232,6 +233,11 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
         pl.bytes[S_SSTATUS] = (size_t)(wa > wc ? wa : wc) * 4;
     }
     pl.bytes[S_PIXC] = pl.bytes[S_PTC] = arrangement == kUntiledKey64 ? (size_t)D * 4 : 0;
+    // Bilinear tiled: the forward blend writes every record it reads, in
+    // tile-list order, so the backward reads its batches sequentially.
+    pl.save_tiled = arrangement == kTiled && o->mode == RAST_SPLAT_BILINEAR &&
+                    (o->flags & RAST_FLAG_SAVE_FOR_BWD) != 0;
+    pl.bytes[S_RECTILE] = pl.save_tiled ? (size_t)D * vt.rec_words * 4 : 0;
     pl.bytes[S_RANGES] = (size_t)ntile * 8;
     pl.bytes[S_ORDER] = (size_t)(ntile + 66) * 4;  // heavy-first order + bucket counts and cursors
     pl.bytes[S_CUTOFF] = (size_t)ntile * 8;
@@ -285,13 +291,15 @@ Bufs make_bufs(const Plan& pl, void* ws) {
     b.last = (uint32_t*)at(S_LAST);
     b.pixC = (uint32_t*)at(S_PIXC);
     b.ptC = (uint32_t*)at(S_PTC);
+    b.rec_tile = pl.save_tiled ? (uint32_t*)at(S_RECTILE) : nullptr;
     b.copy_cap = pl.copy_cap;
     b.blk_cap = pl.blk_cap;
     return b;
 }
 
 __global__ void k_init_header(WsHeader* h, int32_t n_views, long long n_points, long long cap,
-                              long long n_tiles, long long n_pixels) {
+                              long long n_tiles, long long n_pixels, uint32_t rec_tile_valid) {
+    h->rec_tile_valid = rec_tile_valid;
     h->error = 0u;
     h->n_copies = 0u;
     h->n_copies_raw = 0u;
@@ -378,7 +386,7 @@ cudaError_t run_fwd(const Plan& pl, const Bufs& b, cudaStream_t s) {
     {
         ProfScope ps("init_header", s);
         k_init_header<<<1, 1, 0, s>>>(b.hdr, vt.n_views, vt.n_total, pl.copy_cap, vt.tiles_total,
-                                      vt.pix_total);
+                                      vt.pix_total, pl.save_tiled ? 1u : 0u);
         RAST_TRY(cudaGetLastError());
     }
     // The depth sort's first pass generates the point indices itself.
@@ -431,7 +439,7 @@ cudaError_t run_fwd_key64(const Plan& pl, const Bufs& b, cudaStream_t s) {
     {
         ProfScope ps("init_header", s);
         k_init_header<<<1, 1, 0, s>>>(b.hdr, vt.n_views, vt.n_total, pl.copy_cap, vt.tiles_total,
-                                      vt.pix_total);
+                                      vt.pix_total, pl.save_tiled ? 1u : 0u);
         RAST_TRY(cudaGetLastError());
     }
     RAST_TRY(launch_project(vt, b, false, s));

@@ -58,10 +58,18 @@ constexpr int kOpRow = 8;  // floats per point of the dL/do sectors
 template <int TS, int RPT>
 constexpr int stages_for() { return TS == 16 && RPT == 1 ? 3 : 2; }
 
-template <int TS, int RPT, int C, bool BF16>
+// Ring stride (words) of a staged record: padded against bank conflicts when
+// every thread copies its own record; the record stride itself when a batch
+// arrives as one bulk copy of contiguous records (TSRC).
+template <int C, bool BF16, bool TSRC>
+constexpr int bwd_ring_stride() {
+    return TSRC ? RecLayout<0, C, BF16>::words : ring_stride(RecLayout<0, C, BF16>::words);
+}
+
+template <int TS, int RPT, int C, bool BF16, bool TSRC>
 constexpr size_t bilinear_bwd_smem() {
     constexpr int D = TS * TS * RPT;
-    return sizeof(uint32_t) * stages_for<TS, RPT>() * D * ring_stride(RecLayout<0, C, BF16>::words)  // record ring
+    return sizeof(uint32_t) * stages_for<TS, RPT>() * D * bwd_ring_stride<C, BF16, TSRC>()  // record ring
            + sizeof(float) * 4 * 2 * D                                              // (T a, w dL/da) per slot
            + sizeof(float) * TS * TS * C                                            // upstream dL/dF per pixel
            + 128;
@@ -70,10 +78,15 @@ constexpr size_t bilinear_bwd_smem() {
 // RPT = records each thread stages per batch (blend depth D = TS * TS * RPT).
 // 8x8 tiles with one record per thread: held to 64 registers, so the 16 CTAs
 // per SM that shared memory allows stay resident (no spills at that bound).
-template <int TS, int RPT, int C, bool BF16>
+// TSRC: the workspace holds the forward's tile-ordered record copy, so each
+// batch is one contiguous run of records, staged by ONE TMA bulk copy
+// (cp.async.bulk, completed on a per-stage mbarrier) issued by thread 0; if
+// the last forward did not write the copy (header flag), the threads gather
+// the records by point index into the same ring instead.
+template <int TS, int RPT, int C, bool BF16, bool TSRC>
 __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend_bwd_bilinear(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
-    const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec,
+    const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec, const uint32_t* __restrict__ rec_tile,
     const float* __restrict__ t_final, const uint32_t* __restrict__ last_in,
     const uint32_t* __restrict__ base, float* __restrict__ partial, float* __restrict__ grow,
     uint2* __restrict__ cutoff, WsHeader* __restrict__ hdr, unsigned long long* __restrict__ trace) {
@@ -87,7 +100,7 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
     constexpr int PS = partial_stride(P);
     constexpr int GS = grow_stride(P);
     constexpr int RW = RecLayout<0, C, BF16>::words;
-    constexpr int RS = ring_stride(RW);
+    constexpr int RS = bwd_ring_stride<C, BF16, TSRC>();
     constexpr int FW = RecLayout<0, C, BF16>::feat_word;
     extern __shared__ __align__(128) uint32_t s_dyn[];
     uint32_t* const s_ring = align128(s_dyn);                                 // [kStages][D][RS]
@@ -95,12 +108,15 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
     float* const s_da = s_ta + 4 * D;                                         // [4][D]
     float* const s_gF = s_da + 4 * D;                                         // [NT][C]
     __shared__ uint32_t s_mask[NT][MW + 1];
-    __shared__ float s_w[4][D];    // bilinear weight per slot
-    __shared__ float s_inv[4][D];  // 1 / (1 - alpha) per slot
-    __shared__ float s_o[D];       // opacity per record
-    __shared__ float s_z[D];       // depth per record
-    __shared__ uint32_t s_anchor[D];
+    // Per record: the bilinear weights and the 1 / (1 - alpha) of its 2x2
+    // slots, and (tile-local anchor, depth bits, opacity bits). A fragment
+    // reads the three with independent vector loads and picks its slot in
+    // registers, so no shared-memory load waits on another one.
+    __shared__ float4 s_w4[D];
+    __shared__ float4 s_inv4[D];
+    __shared__ uint4 s_azo[D];
     __shared__ uint32_t s_red;
+    __shared__ __align__(8) uint64_t s_mbar[kStages];  // TSRC: one bulk-copy barrier per ring stage
 
     const int64_t tile = order[blockIdx.x];
     const ViewDev& V = vt.v[view_of_tile(vt, tile)];
@@ -130,9 +146,15 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
 #pragma unroll
     for (int c = 0; c < C; ++c) s_gF[tid * C + c] = gF[c];
     // Each thread clears its own mask row; the barriers inside block_max_u32
-    // order these stores before any thread sets bits in another pixel's row.
+    // order these stores before any thread sets bits in another pixel's row
+    // (and the bulk-copy barriers' initialisation before the first copy).
 #pragma unroll
     for (int w = 0; w < MW; ++w) s_mask[tid][w] = 0;
+    if (TSRC && tid == 0) {
+#pragma unroll
+        for (int st = 0; st < kStages; ++st) mbar_init(&s_mbar[st], 1);
+        mbar_init_fence();
+    }
     const uint32_t maxlast = block_max_u32(last, &s_red);
     if (tid == 0 && maxlast) atomicAdd(&hdr->needed_bwd, (unsigned long long)maxlast);
     if (maxlast == 0) {
@@ -154,8 +176,24 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
         const uint32_t q = rg.x + (nb - 1 - j) * D + k * NT + tid;
         return q < end ? pts[q] : 0xffffffffu;
     };
+    // TSRC with the copy written: one bulk copy per batch. Otherwise every
+    // thread gathers its records by point index (cp.async).
+    const bool bulk = TSRC && hdr->rec_tile_valid != 0u;
+    uint32_t phase = 0;        // bulk: parity bit per ring stage
+    uint32_t outstanding = 0;  // bulk: stages with a copy not yet waited for
     auto issue = [&](uint32_t j, const uint32_t (&gi)[RPT]) {
         const int st = (int)(j % kStages);
+        if (bulk) {
+            if (j < nb) {
+                const uint32_t b0 = rg.x + (nb - 1 - j) * D;
+                const uint32_t nrec = end - b0 < (uint32_t)D ? end - b0 : (uint32_t)D;
+                if (tid == 0)
+                    bulk_copy_g2s(s_ring + (size_t)st * D * RS, rec_tile + (size_t)b0 * RW, nrec * RW * 4u,
+                                  &s_mbar[st]);
+                outstanding |= 1u << st;
+            }
+            return;
+        }
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (gi[k] != 0xffffffffu) {
@@ -167,6 +205,7 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
         }
         cp_async_commit();
     };
+    bool failed = false;       // bulk: a copy did not arrive within the poll bound
     uint32_t idx[kStages][RPT];
     uint32_t gi_cur[kStages][RPT];  // point indices per ring slot
 #pragma unroll
@@ -193,7 +232,16 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
             s_ta[k * NT + tid] = 0.f;
             s_da[k * NT + tid] = 0.f;
         }
-        cp_async_wait<kStages - 1>();
+        if (bulk) {
+            if (mbar_wait(&s_mbar[st], (phase >> st) & 1u)) {
+                phase ^= 1u << st;
+                outstanding &= ~(1u << st);
+            } else {
+                failed = true;  // records of this batch may be missing: stop after this barrier round
+            }
+        } else {
+            cp_async_wait<kStages - 1>();
+        }
         // Per staged record: slot rank, anchor, and where its gradient goes.
         int slot_base[RPT], anchor[RPT];
         bool single[RPT];      // the point has this one copy: its gradient is final here
@@ -215,17 +263,15 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
             const float ax = __fsub_rn(1.f, bg.a), by = __fsub_rn(1.f, bg.b);
             const float w0 = __fmul_rn(ax, by), w1 = __fmul_rn(bg.a, by);
             const float w2 = __fmul_rn(ax, bg.b), w3 = __fmul_rn(bg.a, bg.b);
-            s_w[0][r] = w0; s_w[1][r] = w1; s_w[2][r] = w2; s_w[3][r] = w3;
-            s_o[r] = o;
-            s_z[r] = __uint_as_float(g.z);
+            s_w4[r] = make_float4(w0, w1, w2, w3);
             // 1 / (1 - alpha) of each slot, alpha = min(o w, amax) exactly as the forward has it
-            s_inv[0][r] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w0), amax)));
-            s_inv[1][r] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w1), amax)));
-            s_inv[2][r] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w2), amax)));
-            s_inv[3][r] = __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w3), amax)));
+            s_inv4[r] = make_float4(__frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w0), amax))),
+                                    __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w1), amax))),
+                                    __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w2), amax))),
+                                    __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w3), amax))));
             const int X0 = bg.i0 - tx * TS, Y0 = bg.j0 - ty * TS;
             anchor[k] = (X0 + 1) | ((Y0 + 1) << 8);
-            s_anchor[r] = (uint32_t)anchor[k];
+            s_azo[r] = make_uint4((uint32_t)anchor[k], g.z, g.w, 0u);
             const uint32_t bit = 1u << lane;
             const int word = r >> 5;
 #pragma unroll
@@ -266,12 +312,15 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
                 m &= ~(1u << bit);
                 const int r = w * 32 + bit;
                 if (rel0 + r >= last) continue;
-                const uint32_t an = s_anchor[r];
-                const int slot = (lx + 1 - (int)(an & 0xffu)) + 2 * (ly + 1 - (int)(an >> 8));
-                const float wgt = s_w[slot][r];
-                const float ow = __fmul_rn(s_o[r], wgt);
+                const uint4 azo = s_azo[r];
+                const float4 w4 = s_w4[r];
+                const float4 i4 = s_inv4[r];
+                const bool sx = lx + 1 != (int)(azo.x & 0xffu), sy = ly + 1 != (int)(azo.x >> 8);
+                const int slot = (int)sx + 2 * (int)sy;
+                const float wgt = sy ? (sx ? w4.w : w4.z) : (sx ? w4.y : w4.x);
+                const float inv = sy ? (sx ? i4.w : i4.z) : (sx ? i4.y : i4.x);
+                const float ow = __fmul_rn(__uint_as_float(azo.z), wgt);
                 const float alpha = fminf(ow, amax);
-                const float inv = s_inv[slot][r];
                 const float Tk = T * inv;  // T_k = T_{k+1} / (1 - alpha_k)
                 const uint32_t* rp = ring + r * RS;
                 float f[C];
@@ -279,7 +328,7 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
                 float fdot = 0.f;
 #pragma unroll
                 for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], f[c], fdot);
-                const float z = s_z[r];
+                const float z = __uint_as_float(azo.y);
                 const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) * inv;
                 const float ta = Tk * alpha;
                 Sg = fmaf(ta, fdot, Sg);
@@ -291,7 +340,12 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
         }
 #pragma unroll
         for (int w = 0; w < MW; ++w) s_mask[tid][w] = 0;
-        __syncthreads();
+        if (__syncthreads_or(failed)) {
+            // A bulk copy did not arrive in time: report it and stop (every
+            // thread leaves here together; nothing is written from this batch).
+            if (tid == 0) atomicOr(&hdr->error, kErrTimeout);
+            break;
+        }
         // Slot st is free (every pixel is done with it): refill it with iteration j + kStages.
         issue(j + kStages, idx[0]);
 #pragma unroll
@@ -356,6 +410,11 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
         // come after its first barrier, which every reader here precedes.
     }
     cp_async_wait<0>();
+    // No bulk copy may land after the CTA has exited: wait (bounded) for any
+    // the loop did not consume (only after a timeout).
+#pragma unroll
+    for (int st = 0; st < kStages; ++st)
+        if ((outstanding >> st) & 1u) mbar_wait(&s_mbar[st], (phase >> st) & 1u);
     if (tid == 0) trace_tile(trace, tile, 1, t_start, c_start);
 }
 
@@ -405,7 +464,7 @@ constexpr size_t gauss_bwd_smem() {
 // After a barrier each record's loader thread adds the rows of the warps that
 // hit it, in warp order, and writes the copy's partial row.
 template <int TS, int C, bool BF16>
-__global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
+__global__ void __launch_bounds__(TS * TS, 1024 / (TS * TS)) k_blend_bwd_gauss(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec,
     const float* __restrict__ t_final, const uint32_t* __restrict__ last_in,
@@ -793,21 +852,31 @@ __global__ void __launch_bounds__(256, 6) k_reduce_grads(const ViewTable vt, con
     if (V.d_scale) V.d_scale[i] = V.scale ? gs : 0.f;
 }
 
+template <int TS, int RPT, int C, bool BF16, bool TSRC>
+cudaError_t launch_bwd_bilinear(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    const unsigned grid = (unsigned)vt.tiles_total;
+    constexpr size_t smem = bilinear_bwd_smem<TS, RPT, C, BF16, TSRC>();
+    static PerDevice attr;
+    const cudaError_t e = per_device(attr, nullptr, [](int, int*) {
+        return cudaFuncSetAttribute(k_blend_bwd_bilinear<TS, RPT, C, BF16, TSRC>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (e != cudaSuccess) return e;
+    ProfScope ps("blend_bwd", s);
+    k_blend_bwd_bilinear<TS, RPT, C, BF16, TSRC><<<grid, TS * TS, smem, s>>>(
+        vt, b.ranges, b.order, pts, b.rec, b.rec_tile, b.t_final, b.last, b.base, b.partial, b.grow, b.cutoff,
+        b.hdr, b.trace);
+    return cudaGetLastError();
+}
+
 template <int TS, int RPT, int C, bool BF16>
 cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     const unsigned grid = (unsigned)vt.tiles_total;
     if (vt.mode == 0) {
-        constexpr size_t smem = bilinear_bwd_smem<TS, RPT, C, BF16>();
-        static PerDevice attr;
-        const cudaError_t e = per_device(attr, nullptr, [](int, int*) {
-            return cudaFuncSetAttribute(k_blend_bwd_bilinear<TS, RPT, C, BF16>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        });
-        if (e != cudaSuccess) return e;
-        ProfScope ps("blend_bwd", s);
-        k_blend_bwd_bilinear<TS, RPT, C, BF16><<<grid, TS * TS, smem, s>>>(
-            vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.grow, b.cutoff, b.hdr,
-            b.trace);
+        // With the forward's tile-ordered record copy in the workspace, the
+        // batches are staged by bulk copies.
+        if (b.rec_tile) return launch_bwd_bilinear<TS, RPT, C, BF16, true>(vt, b, pts, s);
+        return launch_bwd_bilinear<TS, RPT, C, BF16, false>(vt, b, pts, s);
     } else {
         constexpr size_t smem = gauss_bwd_smem<TS, C>();
         static PerDevice attr;

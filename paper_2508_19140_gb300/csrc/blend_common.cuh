@@ -44,6 +44,54 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// ---- TMA bulk copies completed on an mbarrier ---------------------------------
+// One thread arms the barrier with the batch's byte count and issues a single
+// global -> shared bulk copy of a contiguous run of records; every thread then
+// waits on the barrier's phase. Each wait is bounded: after kMbarPolls polls
+// it reports failure (the caller raises the timeout bit of the error word and
+// stops) instead of spinning on.
+
+constexpr uint32_t kMbarPolls = 1u << 20;
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes the barriers' initialisation visible to the copy engine (follow with
+// a CTA barrier before the first copy).
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arms `bar` for `bytes` and copies them from global `src` to shared `dst`
+// (both 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    const uint32_t b = smem_addr(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+
+// Waits until the phase of `bar` with this parity has completed; false if it
+// did not within kMbarPolls polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t b = smem_addr(bar);
+    for (uint32_t i = 0; i < kMbarPolls; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // Record stride (u32 words) for a mode, channel count and feature type; the
 // host computes the same value (rec_words). A power of two of at least 8
 // words (32 bytes): every record is 16-byte aligned for cp.async and no record

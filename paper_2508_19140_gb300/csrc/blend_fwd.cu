@@ -108,8 +108,9 @@ constexpr size_t bilinear_fwd_smem() {
 template <int TS, int RPT, int C, bool BF16>
 __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
-    const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec, float* __restrict__ t_final,
-    uint32_t* __restrict__ last_out, WsHeader* __restrict__ hdr, unsigned long long* __restrict__ trace) {
+    const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec, uint32_t* __restrict__ rec_tile,
+    float* __restrict__ t_final, uint32_t* __restrict__ last_out, WsHeader* __restrict__ hdr,
+    unsigned long long* __restrict__ trace) {
     constexpr int NT = TS * TS;     // threads = pixels
     constexpr int D = NT * RPT;     // records per batch
     constexpr int MW = D / 32;      // mask words per pixel
@@ -122,9 +123,12 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     extern __shared__ __align__(128) uint32_t s_dyn[];
     uint32_t* const s_ring = align128(s_dyn);  // [kStages][D][RS] raw records
     __shared__ uint32_t s_mask[NT][MW + 1];    // MW words + 1 pad: conflict-free row reads
-    __shared__ float s_alpha[4][D];            // alpha of each record's 2x2 slots (FP32, pinned ops)
-    __shared__ uint32_t s_anchor[D];           // tile-local anchor (X0 + 1) | (Y0 + 1) << 8
-    __shared__ float s_z[D];                   // depth per record (one word per bank-spread slot)
+    // Per record: the alphas of its 2x2 slots (FP32, pinned ops) and (tile-local
+    // anchor (X0 + 1) | (Y0 + 1) << 8, depth bits). A fragment reads both with
+    // two independent vector loads and picks its slot's alpha in registers, so
+    // no shared-memory load waits on another one.
+    __shared__ float4 s_alpha4[D];
+    __shared__ uint2 s_az[D];
     __shared__ uint32_t s_maxstop;
 
     const int64_t tile = order[blockIdx.x];
@@ -196,16 +200,24 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
                 // bilin_weight and the clamp, so every pixel sees the same FP32
                 // bits) and one mask bit per covered pixel of this tile.
                 const uint4 g = *reinterpret_cast<const uint4*>(ring + r * RS);
+                if (rec_tile) {
+                    // The record, in list order, for the backward's sequential reads
+                    // (coalesced: consecutive threads write consecutive records).
+                    uint4* dst = reinterpret_cast<uint4*>(rec_tile + (size_t)(rg.x + rel0 + r) * RW);
+                    dst[0] = g;
+#pragma unroll
+                    for (int q = 1; q < RW / 4; ++q)
+                        dst[q] = *reinterpret_cast<const uint4*>(ring + r * RS + 4 * q);
+                }
                 const BilinGeom bg = bilin_geom(__uint_as_float(g.x), __uint_as_float(g.y));
                 const float o = __uint_as_float(g.w);
                 const float ax = __fsub_rn(1.f, bg.a), by = __fsub_rn(1.f, bg.b);
-                s_alpha[0][r] = fminf(__fmul_rn(o, __fmul_rn(ax, by)), amax);
-                s_alpha[1][r] = fminf(__fmul_rn(o, __fmul_rn(bg.a, by)), amax);
-                s_alpha[2][r] = fminf(__fmul_rn(o, __fmul_rn(ax, bg.b)), amax);
-                s_alpha[3][r] = fminf(__fmul_rn(o, __fmul_rn(bg.a, bg.b)), amax);
+                s_alpha4[r] = make_float4(fminf(__fmul_rn(o, __fmul_rn(ax, by)), amax),
+                                          fminf(__fmul_rn(o, __fmul_rn(bg.a, by)), amax),
+                                          fminf(__fmul_rn(o, __fmul_rn(ax, bg.b)), amax),
+                                          fminf(__fmul_rn(o, __fmul_rn(bg.a, bg.b)), amax));
                 const int X0 = bg.i0 - tx * TS, Y0 = bg.j0 - ty * TS;
-                s_anchor[r] = (uint32_t)(X0 + 1) | ((uint32_t)(Y0 + 1) << 8);
-                s_z[r] = __uint_as_float(g.z);
+                s_az[r] = make_uint2((uint32_t)(X0 + 1) | ((uint32_t)(Y0 + 1) << 8), g.z);
                 const uint32_t bit = 1u << lane;
                 const int word = r >> 5;
 #pragma unroll
@@ -231,9 +243,10 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
                 if (m == 0) break;
                 const int r = w * 32 + __ffs(m) - 1;
                 m &= m - 1;
-                const uint32_t an = s_anchor[r];
-                const int slot = (lx + 1 - (int)(an & 0xffu)) + 2 * (ly + 1 - (int)(an >> 8));
-                const float alpha = s_alpha[slot][r];
+                const uint2 az = s_az[r];
+                const float4 a4 = s_alpha4[r];
+                const bool sx = lx + 1 != (int)(az.x & 0xffu), sy = ly + 1 != (int)(az.x >> 8);
+                const float alpha = sy ? (sx ? a4.w : a4.z) : (sx ? a4.y : a4.x);
                 const float nT = __fmul_rn(T, __fsub_rn(1.f, alpha));
                 if (nT < tmin) {
                     done = true;
@@ -246,7 +259,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
                 const float ta = T * alpha;
 #pragma unroll
                 for (int c = 0; c < C; ++c) F[c] = fmaf(ta, f[c], F[c]);
-                Dp = fmaf(ta, s_z[r], Dp);
+                Dp = fmaf(ta, __uint_as_float(az.y), Dp);
                 A += ta;
                 T = nT;
                 last = rel0 + r + 1;
@@ -441,7 +454,7 @@ cudaError_t launch_fwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts
         if (e != cudaSuccess) return e;
         ProfScope ps("blend_fwd", s);
         k_blend_fwd_bilinear<TS, RPT, C, BF16><<<grid, TS * TS, smem, s>>>(
-            vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.hdr, b.trace);
+            vt, b.ranges, b.order, pts, b.rec, b.rec_tile, b.t_final, b.last, b.hdr, b.trace);
         return cudaGetLastError();
     }
     ProfScope ps("blend_fwd", s);

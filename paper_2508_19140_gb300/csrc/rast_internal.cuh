@@ -74,7 +74,9 @@ struct WsHeader {
     unsigned long long needed;      // records the forward blend had to read
     unsigned long long needed_bwd;  // records the backward replay read
     long long n_points, copy_cap, n_tiles, n_pixels;
-    long long pad[2];
+    uint32_t rec_tile_valid;  // the last forward wrote the tile-ordered record copy
+    uint32_t pad0;
+    long long pad1;
 };
 
 // ---- small device helpers --------------------------------------------------
@@ -193,6 +195,7 @@ struct ProfScope {
 struct Bufs {
     // per point
     uint32_t* rec;        // records, rec_words per point
+    uint32_t* rec_tile;   // bilinear: the records the forward blend read, in tile-list order (per copy)
     uint2* rect;          // tile rect per point
     uint32_t* cnt;        // copies per point (point order)
     uint32_t* zbits;      // FP32 bits of the view depth per point (backward bookkeeping)

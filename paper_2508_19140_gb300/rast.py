@@ -32,6 +32,7 @@ GAUSS_EWA, GAUSS_ISO = 0, 1
 F32, BF16 = 0, 1
 PASS_FWD, PASS_BWD = 1, 2
 FLAG_TEST_SORT_STALL = 1  # RAST_FLAG_TEST_SORT_STALL: failure-path tests only
+FLAG_SAVE_FOR_BWD = 2     # RAST_FLAG_SAVE_FOR_BWD: the forward keeps a tile-ordered record copy for the backward
 
 
 class RastError(RuntimeError):
@@ -462,6 +463,9 @@ class _Batch(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, cams, opts_kw, check, n_views, *flat):
+        if any(ctx.needs_input_grad[4:]):
+            # a backward will follow: keep the tile-ordered record copy for it
+            opts_kw = dict(opts_kw, flags=int(opts_kw.get("flags", 0)) | FLAG_SAVE_FOR_BWD)
         opts = make_opts(**opts_kw)
         dev = flat[0].device
         pts, views, outs = [], [], []

@@ -73,7 +73,7 @@ def test_autotune_times_each_candidate_and_caches(lib, tmp_path):
         return fake[(opts.tile, opts.blend_depth)]
 
     r = autotune.autotune(vs, o, 3, device_name="GB300", timer=timer, cache_file=cache)
-    assert (r.tile, r.blend_depth, r.from_cache) == (8, 64, False)
+    assert (r.tile, r.blend_depth, r.from_cache, r.save_copy) == (8, 64, False, False)
     assert seen == list(fake)
     assert (o.tile, o.blend_depth) == (16, 0)  # caller's opts untouched
     d = json.load(open(cache))
@@ -102,3 +102,35 @@ def test_no_candidate_runs(lib, tmp_path):
     with pytest.raises(RuntimeError):
         autotune.autotune(_views([(64, 64, 10)]), rast.make_opts(), 1, device_name="X",
                           timer=lambda o: None, cache_file=str(tmp_path / "t.json"))
+
+
+def test_record_copy_is_a_tuned_choice_when_allowed(lib, tmp_path):
+    """With RAST_FLAG_SAVE_FOR_BWD in the caller's opts and a backward pass,
+    every pair is timed without and then with the record copy; the flag of
+    the winner is what with_split applies. Without the caller's flag, or for
+    a forward-only pass, the copy is never tried."""
+    cache = str(tmp_path / "tune.json")
+    vs = _views([(1280, 832, 4 << 20)], C=4, bf16=False)
+    o = rast.make_opts(flags=rast.FLAG_SAVE_FOR_BWD)
+    seen = []
+
+    def timer(opts):
+        save = bool(opts.flags & rast.FLAG_SAVE_FOR_BWD)
+        seen.append((opts.tile, opts.blend_depth, save))
+        return 2.0 if (opts.tile, opts.blend_depth, save) == (8, 64, True) else 3.0
+
+    r = autotune.autotune(vs, o, 3, device_name="GB300", timer=timer, cache_file=cache)
+    pairs = rast.rasterize_tune_candidates("bilinear")
+    assert seen == [(t, d, False) for t, d in pairs] + [(t, d, True) for t, d in pairs]
+    assert (r.tile, r.blend_depth, r.save_copy) == (8, 64, True)
+    o2 = autotune.with_split(o, r.tile, r.blend_depth, r.save_copy)
+    assert o2.flags & rast.FLAG_SAVE_FOR_BWD
+    assert not autotune.with_split(o, 8, 64, False).flags & rast.FLAG_SAVE_FOR_BWD
+    r2 = autotune.autotune(vs, o, 3, device_name="GB300", timer=None, cache_file=cache)
+    assert (r2.from_cache, r2.save_copy) == (True, True)
+    seen.clear()
+    autotune.autotune(vs, rast.make_opts(), 3, device_name="X", timer=timer, use_cache=False)
+    assert all(not s for _, _, s in seen)
+    seen.clear()
+    autotune.autotune(vs, o, 1, device_name="X", timer=timer, use_cache=False)
+    assert all(s for _, _, s in seen) and len(seen) == len(pairs)

@@ -269,6 +269,28 @@ def test_deterministic_rerun(name, bf16):
             assert np.array_equal(val, r.grads()[key]), key
 
 
+# ----------------------------------------------------------------------------- saved record copy
+
+@pytest.mark.parametrize("name,tile,depth", [("dense", 8, 64), ("ragged", 16, 0), ("tiny", 8, 256),
+                                             ("dense", 16, 512)])
+def test_saved_record_copy_gives_same_bits(name, tile, depth):
+    """With RAST_FLAG_SAVE_FOR_BWD the forward writes the records it reads in
+    tile-list order and the backward reads them from there instead of
+    gathering them by point index: images and gradients are the same bits
+    (also on a workspace pre-filled with 0xFF, and with BF16 features)."""
+    from paper_2508_19140_gb300 import rast
+    v = case_view(name)
+    for bf16 in (False, True):
+        a = Run([v], backward=True, bf16=bf16, tile=tile, blend_depth=depth)
+        b = Run([v], backward=True, bf16=bf16, tile=tile, blend_depth=depth, ws_fill=0xFF,
+                flags=rast.FLAG_SAVE_FOR_BWD)
+        assert a.status == 0 and b.status == 0
+        for x, y in zip(a.image(), b.image()):
+            assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+        for key, val in a.grads().items():
+            assert np.array_equal(val.view(np.uint32), b.grads()[key].view(np.uint32)), key
+
+
 # ----------------------------------------------------------------------------- stale workspace
 
 @pytest.mark.parametrize("name,tile,depth", [("tiny", 16, 0), ("dense", 8, 64), ("ragged", 8, 64),
