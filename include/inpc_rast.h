@@ -187,8 +187,8 @@ rast_status_t rasterize_fwd(const rast_points_t* pts, const rast_camera_t* cam,
  * The intermediate arrays live in one static device array of 16 MiB
  * (1 << 24 bytes) that every GPU loading the library keeps until exit;
  * problems whose rasterize_workspace_size() exceeds it return
- * RAST_ERR_CAPACITY before any device work (e.g. 65,536 points at 256x256
- * with 4 f32 features fit). The first call on a device looks up the array's
+ * RAST_ERR_CAPACITY before any device work (e.g. up to 53,888 points at
+ * 256x256 with 4 f32 features fit). The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture. Every call reuses the same array and
  * finds the previous call's contents there (the forward clears what it needs

@@ -107,9 +107,10 @@ def candidates_for(opts, passes: int, pairs) -> list:
     flag has it, and, when the copy can matter (bilinear, a backward, the
     caller allows it), every pair again with the copy."""
     allow = bool(int(opts.flags) & rast.FLAG_SAVE_FOR_BWD)
-    if allow and (passes & rast.PASS_BWD) and int(opts.mode) == rast.BILINEAR:
+    bilinear = int(opts.mode) == rast.BILINEAR
+    if allow and (passes & rast.PASS_BWD) and bilinear:
         return [(t, d, False) for t, d in pairs] + [(t, d, True) for t, d in pairs]
-    return [(t, d, allow) for t, d in pairs]
+    return [(t, d, allow and bilinear) for t, d in pairs]  # Gaussian mode keeps no record copy
 
 
 def load_cache(path: str | None = None) -> dict:

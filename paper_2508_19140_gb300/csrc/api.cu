@@ -158,6 +158,8 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
         d.H = c.height;
         d.tiles_x = (c.width + T - 1) / T;
         d.tiles_y = (c.height + T - 1) / T;
+        // Bilinear rects are packed into 32 bits (14 bits of tile row).
+        if (o->mode == RAST_SPLAT_BILINEAR && d.tiles_y > kRect4MaxTilesY) return RAST_ERR_NOT_SUPPORTED;
         d.key_base = f32_bits(c.near_z);
         d.key_cull = f32_bits(c.far_z) - f32_bits(c.near_z);
         if (d.key_cull > max_cull) max_cull = d.key_cull;
@@ -265,6 +267,7 @@ Bufs make_bufs(const Plan& pl, void* ws) {
     b.hdr = (WsHeader*)at(S_HDR);
     b.rec = (uint32_t*)at(S_REC);
     b.rect = (uint2*)at(S_RECT);
+    b.rect4 = (uint32_t*)at(S_RECT);
     b.cnt = (uint32_t*)at(S_CNT);
     b.zbits = (uint32_t*)at(S_ZBITS);
     b.keyA[0] = (uint32_t*)at(S_KEYA0);
@@ -272,6 +275,7 @@ Bufs make_bufs(const Plan& pl, void* ws) {
     b.valA[0] = (uint32_t*)at(S_VALA0);
     b.valA[1] = (uint32_t*)at(S_VALA1);
     b.rectS = (uint2*)at(S_RECTS);
+    b.rect4S = (uint32_t*)at(S_RECTS);
     b.base = (uint32_t*)at(S_BASE);
     b.blk = (uint32_t*)at(S_BLK);
     b.keyC[0] = (uint32_t*)at(S_KEYC0);

@@ -464,7 +464,7 @@ constexpr size_t gauss_bwd_smem() {
 // After a barrier each record's loader thread adds the rows of the warps that
 // hit it, in warp order, and writes the copy's partial row.
 template <int TS, int C, bool BF16>
-__global__ void __launch_bounds__(TS * TS, 1024 / (TS * TS)) k_blend_bwd_gauss(
+__global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec,
     const float* __restrict__ t_final, const uint32_t* __restrict__ last_in,
@@ -674,6 +674,7 @@ __global__ void __launch_bounds__(TS * TS, 1024 / (TS * TS)) k_blend_bwd_gauss(
 template <int C, int MODE>
 __global__ void __launch_bounds__(256, 6) k_reduce_grads(const ViewTable vt, const uint32_t* __restrict__ zbits,
                                                       const uint2* __restrict__ rect,
+                                                      const uint32_t* __restrict__ rect4,
                                                       const uint32_t* __restrict__ base,
                                                       const uint2* __restrict__ cutoff,
                                                       const float* __restrict__ partial,
@@ -689,7 +690,7 @@ __global__ void __launch_bounds__(256, 6) k_reduce_grads(const ViewTable vt, con
 #pragma unroll
     for (int k = 0; k < P; ++k) acc[k] = 0.f;
     // Independent loads first: one memory round trip for all three.
-    const uint2 rc = rect[gi];
+    const uint2 rc = MODE == 0 ? rect4_unpack(rect4[gi]) : rect[gi];
     const uint32_t zb = zbits[gi];
     const uint32_t pbase = base[gi];
     const uint32_t cnt = rect_count(rc);
@@ -914,9 +915,9 @@ cudaError_t launch_reduce_c(const ViewTable& vt, const Bufs& b, cudaStream_t s) 
     const unsigned grid = (unsigned)((vt.n_total + 255) / 256);
     ProfScope ps("reduce_grads", s);
     if (vt.mode == 0)
-        k_reduce_grads<C, 0><<<grid, 256, 0, s>>>(vt, b.zbits, b.rect, b.base, b.cutoff, b.partial, b.grow);
+        k_reduce_grads<C, 0><<<grid, 256, 0, s>>>(vt, b.zbits, b.rect, b.rect4, b.base, b.cutoff, b.partial, b.grow);
     else
-        k_reduce_grads<C, 1><<<grid, 256, 0, s>>>(vt, b.zbits, b.rect, b.base, b.cutoff, b.partial, b.grow);
+        k_reduce_grads<C, 1><<<grid, 256, 0, s>>>(vt, b.zbits, b.rect, b.rect4, b.base, b.cutoff, b.partial, b.grow);
     return cudaGetLastError();
 }
 

@@ -79,24 +79,45 @@ __device__ __forceinline__ void store_rects(uint2* __restrict__ p, int64_t s0, i
 // k_dup_write) and the block's copy count. If the depth sort failed (its
 // look-back wait ran out: the error word is set before this kernel starts),
 // every point counts as empty, so no copy is made from a partial order; an
-// index outside [0, n) is treated the same way.
+// index outside [0, n) is treated the same way. P4: bilinear packed 4-byte
+// rects (the gather's array is half the size).
+template <bool P4>
 __global__ void __launch_bounds__(kT) k_dup_count(const uint32_t* __restrict__ sorted_pts,
-                                                  const uint2* __restrict__ rect,
-                                                  uint2* __restrict__ rectS, int64_t n,
-                                                  uint32_t* __restrict__ blk, const WsHeader* __restrict__ hdr) {
+                                                  const void* __restrict__ rect, void* __restrict__ rectS,
+                                                  int64_t n, uint32_t* __restrict__ blk,
+                                                  const WsHeader* __restrict__ hdr) {
     __shared__ uint32_t s_warp[33];
     const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
     const bool failed = (hdr->error & kErrTimeout) != 0u;
     uint32_t gi[kPer];
     load_u32s(sorted_pts, s0, n, gi, 0xffffffffu);
-    uint2 r[kPer];
-#pragma unroll
-    for (int j = 0; j < kPer; ++j)
-        r[j] = (!failed && (int64_t)gi[j] < n) ? rect[gi[j]] : make_uint2(1u, 0u);
     uint32_t c = 0;
+    if constexpr (P4) {
+        const uint32_t* r4 = static_cast<const uint32_t*>(rect);
+        uint32_t r[kPer];
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) c += rect_count(r[j]);
-    store_rects(rectS, s0, n, r);
+        for (int j = 0; j < kPer; ++j) r[j] = (!failed && (int64_t)gi[j] < n) ? r4[gi[j]] : kRect4Empty;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) c += rect4_count(r[j]);
+        uint32_t* out = static_cast<uint32_t*>(rectS);
+        if (s0 + kPer <= n) {
+#pragma unroll
+            for (int j = 0; j < kPer; j += 4)
+                *reinterpret_cast<uint4*>(out + s0 + j) = make_uint4(r[j], r[j + 1], r[j + 2], r[j + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j)
+                if (s0 + j < n) out[s0 + j] = r[j];
+        }
+    } else {
+        const uint2* r8 = static_cast<const uint2*>(rect);
+        uint2 r[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) r[j] = (!failed && (int64_t)gi[j] < n) ? r8[gi[j]] : make_uint2(1u, 0u);
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) c += rect_count(r[j]);
+        store_rects(static_cast<uint2*>(rectS), s0, n, r);
+    }
     uint32_t tot;
     block_excl_scan<kT>(c, s_warp, tot);
     if (threadIdx.x == 0) blk[blockIdx.x] = tot;
@@ -153,9 +174,11 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ blk
 // are the long part here, so more threads beat more items per thread).
 constexpr int kTW = 2 * kT;
 constexpr int kPerW = kScanItems / kTW;
+static_assert(kPerW == 4, "the packed-rect path loads four rects as one 16-byte vector");
 
+template <bool P4>
 __global__ void __launch_bounds__(kTW) k_dup_write(const ViewTable vt, const uint32_t* __restrict__ sorted_pts,
-                                                   const uint2* __restrict__ rectS, int64_t n,
+                                                   const void* __restrict__ rectS, int64_t n,
                                                    const uint32_t* __restrict__ blk,
                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                    int64_t cap) {
@@ -164,11 +187,17 @@ __global__ void __launch_bounds__(kTW) k_dup_write(const ViewTable vt, const uin
     uint2 r[kPerW];
     uint32_t gi[kPerW];
     if (s0 + kPerW <= n) {
+        if constexpr (P4) {
+            const uint4 q = *reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(rectS) + s0);
+            r[0] = rect4_unpack(q.x); r[1] = rect4_unpack(q.y); r[2] = rect4_unpack(q.z); r[3] = rect4_unpack(q.w);
+        } else {
+            const uint2* rs = static_cast<const uint2*>(rectS);
 #pragma unroll
-        for (int j = 0; j < kPerW; j += 2) {
-            const uint4 q = *reinterpret_cast<const uint4*>(rectS + s0 + j);
-            r[j] = make_uint2(q.x, q.y);
-            r[j + 1] = make_uint2(q.z, q.w);
+            for (int j = 0; j < kPerW; j += 2) {
+                const uint4 q = *reinterpret_cast<const uint4*>(rs + s0 + j);
+                r[j] = make_uint2(q.x, q.y);
+                r[j + 1] = make_uint2(q.z, q.w);
+            }
         }
 #pragma unroll
         for (int j = 0; j < kPerW; j += 4) {
@@ -179,7 +208,8 @@ __global__ void __launch_bounds__(kTW) k_dup_write(const ViewTable vt, const uin
 #pragma unroll
         for (int j = 0; j < kPerW; ++j) {
             const bool ok = s0 + j < n;
-            r[j] = ok ? rectS[s0 + j] : make_uint2(1u, 0u);
+            if constexpr (P4) r[j] = ok ? rect4_unpack(static_cast<const uint32_t*>(rectS)[s0 + j]) : make_uint2(1u, 0u);
+            else r[j] = ok ? static_cast<const uint2*>(rectS)[s0 + j] : make_uint2(1u, 0u);
             gi[j] = ok ? sorted_pts[s0 + j] : 0u;
         }
     }
@@ -278,14 +308,14 @@ __global__ void __launch_bounds__(kT) k_ranges(const uint32_t* __restrict__ keys
 // stable LSD radix sort over the 64-bit key [pixel | depth] then yields the
 // per-pixel lists in (depth, point index) order, ties falling back to the
 // point order the copies were written in.
-__global__ void __launch_bounds__(kT) k_untiled_copies(const ViewTable vt, const uint2* __restrict__ rect,
+__global__ void __launch_bounds__(kT) k_untiled_copies(const ViewTable vt, const uint32_t* __restrict__ rect4,
                                                        const uint32_t* __restrict__ dkey,
                                                        const uint32_t* __restrict__ base,
                                                        uint32_t* __restrict__ key_lo, uint32_t* __restrict__ key_hi,
                                                        uint32_t* __restrict__ pt, int64_t cap) {
     const int64_t gi = (int64_t)blockIdx.x * kT + threadIdx.x;
     if (gi >= vt.n_total) return;
-    const uint2 r = rect[gi];
+    const uint2 r = rect4_unpack(rect4[gi]);  // bilinear only: packed rects
     if (rect_count(r) == 0) return;
     const ViewDev& V = vt.v[view_of_point(vt, gi)];
     const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff, y1 = r.y >> 16;
@@ -337,7 +367,7 @@ cudaError_t launch_untiled_copies(const ViewTable& vt, const Bufs& b, const uint
     }
     {
         ProfScope ps("dup.write", s);
-        k_untiled_copies<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(vt, b.rect, dkey, b.base, key_lo, key_hi, pt,
+        k_untiled_copies<<<(unsigned)((n + kT - 1) / kT), kT, 0, s>>>(vt, b.rect4, dkey, b.base, key_lo, key_hi, pt,
                                                                       b.copy_cap);
     }
     return cudaGetLastError();
@@ -361,7 +391,8 @@ cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t*
     if (nb == 0) return cudaSuccess;  // the header was zeroed at the start of the pass
     {
         ProfScope ps("dup.count", s);
-        k_dup_count<<<(unsigned)nb, kT, 0, s>>>(sorted_pts, b.rect, b.rectS, n, b.blk, b.hdr);
+        if (vt.mode == 0) k_dup_count<true><<<(unsigned)nb, kT, 0, s>>>(sorted_pts, b.rect4, b.rect4S, n, b.blk, b.hdr);
+        else k_dup_count<false><<<(unsigned)nb, kT, 0, s>>>(sorted_pts, b.rect, b.rectS, n, b.blk, b.hdr);
     }
     {
         ProfScope ps("dup.scan", s);
@@ -369,8 +400,12 @@ cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t*
     }
     {
         ProfScope ps("dup.write", s);
-        k_dup_write<<<(unsigned)nb, kTW, 0, s>>>(vt, sorted_pts, b.rectS, n, b.blk, b.keyC[0],
-                                               b.valC[0], b.copy_cap);
+        if (vt.mode == 0)
+            k_dup_write<true><<<(unsigned)nb, kTW, 0, s>>>(vt, sorted_pts, b.rect4S, n, b.blk, b.keyC[0],
+                                                         b.valC[0], b.copy_cap);
+        else
+            k_dup_write<false><<<(unsigned)nb, kTW, 0, s>>>(vt, sorted_pts, b.rectS, n, b.blk, b.keyC[0],
+                                                          b.valC[0], b.copy_cap);
     }
     return cudaGetLastError();
 }

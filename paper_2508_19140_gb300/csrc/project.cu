@@ -151,7 +151,12 @@ __global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs 
     }
     b.keyA[0][gi] = key;
     if (write_vals) b.valA[0][gi] = (uint32_t)gi;
-    b.rect[gi] = rect;
+    if (MODE == 0)
+        b.rect4[gi] = vis ? rect4_pack((int)(rect.x & 0xffffu), (int)(rect.x >> 16), (int)(rect.y & 0xffffu),
+                                       (int)(rect.y >> 16))
+                          : kRect4Empty;
+    else
+        b.rect[gi] = rect;
     b.cnt[gi] = count;
     b.zbits[gi] = __float_as_uint(zc);
 }

@@ -141,6 +141,29 @@ __host__ __device__ constexpr int partial_stride(int P) { return (P + 3) & ~3; }
 // neighbour's bytes.
 __host__ __device__ constexpr int grow_stride(int P) { return P <= 4 ? 4 : (P <= 8 ? 8 : (P <= 16 ? 16 : 32)); }
 
+// Bilinear footprints (2x2 pixels) touch at most 2x2 tiles, so their rect
+// packs into 32 bits: tx0 (16 bits) | ty0 (14 bits) << 16 | (tx1 - tx0) << 30
+// | (ty1 - ty0) << 31; empty = all ones (tx0 = 0xffff is never a tile
+// column: tiles_x <= 65535). Half the bytes of the gather in depth order that
+// the duplication makes, so twice as much of the array stays in L2.
+constexpr uint32_t kRect4Empty = 0xffffffffu;
+constexpr int kRect4MaxTilesY = 1 << 14;
+
+__device__ __forceinline__ uint32_t rect4_pack(int tx0, int ty0, int tx1, int ty1) {
+    return (uint32_t)tx0 | ((uint32_t)ty0 << 16) | ((uint32_t)(tx1 - tx0) << 30) | ((uint32_t)(ty1 - ty0) << 31);
+}
+
+__device__ __forceinline__ uint2 rect4_unpack(uint32_t p) {
+    if (p == kRect4Empty) return make_uint2(1u, 0u);
+    const uint32_t tx0 = p & 0xffffu, ty0 = (p >> 16) & 0x3fffu;
+    const uint32_t tx1 = tx0 + ((p >> 30) & 1u), ty1 = ty0 + (p >> 31);
+    return make_uint2(tx0 | (ty0 << 16), tx1 | (ty1 << 16));
+}
+
+__device__ __forceinline__ uint32_t rect4_count(uint32_t p) {
+    return p == kRect4Empty ? 0u : (1u + ((p >> 30) & 1u)) * (1u + (p >> 31));
+}
+
 __device__ __forceinline__ uint32_t rect_count(uint2 r) {
     const int tx0 = r.x & 0xffff, ty0 = r.x >> 16, tx1 = r.y & 0xffff, ty1 = r.y >> 16;
     if (tx1 < tx0 || ty1 < ty0) return 0;
@@ -196,12 +219,14 @@ struct Bufs {
     // per point
     uint32_t* rec;        // records, rec_words per point
     uint32_t* rec_tile;   // bilinear: the records the forward blend read, in tile-list order (per copy)
-    uint2* rect;          // tile rect per point
+    uint2* rect;          // tile rect per point (Gaussian; bilinear: rect4)
+    uint32_t* rect4;      // bilinear: packed tile rect per point (same memory as rect)
     uint32_t* cnt;        // copies per point (point order)
     uint32_t* zbits;      // FP32 bits of the view depth per point (backward bookkeeping)
     uint32_t* keyA[2];    // depth sort ping-pong
     uint32_t* valA[2];
-    uint2* rectS;         // rects in depth order
+    uint2* rectS;         // rects in depth order (Gaussian; bilinear: rect4S)
+    uint32_t* rect4S;     // bilinear: packed rects in depth order (same memory as rectS)
     uint32_t* blk;        // block sums for scans
     uint32_t* base;       // point-order exclusive scan of cnt (backward)
     // per copy

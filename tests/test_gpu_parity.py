@@ -85,10 +85,17 @@ def test_records_and_rects_bit_exact(name):
         for k in range(3):
             assert np.array_equal(rec[vis, 4 + k], f32(p["conic"][vis, k]))
     n = len(v.xyz)
-    rect = r.arr("rect", np.uint32, 2 * n).reshape(n, 2)
     box = p["box"]
-    tx0, ty0 = rect[:, 0] & 0xFFFF, rect[:, 0] >> 16
-    tx1, ty1 = rect[:, 1] & 0xFFFF, rect[:, 1] >> 16
+    if mode == "gaussian":
+        rect = r.arr("rect", np.uint32, 2 * n).reshape(n, 2)
+        tx0, ty0 = rect[:, 0] & 0xFFFF, rect[:, 0] >> 16
+        tx1, ty1 = rect[:, 1] & 0xFFFF, rect[:, 1] >> 16
+    else:
+        # bilinear rects are packed: tx0 | ty0 << 16 | (tx1 - tx0) << 30 | (ty1 - ty0) << 31
+        p4 = r.arr("rect", np.uint32, n).astype(np.int64)
+        tx0, ty0 = p4 & 0xFFFF, (p4 >> 16) & 0x3FFF
+        tx1, ty1 = tx0 + ((p4 >> 30) & 1), ty0 + (p4 >> 31)
+        assert np.all(p4[~vis] == 0xFFFFFFFF)
     assert np.array_equal(tx0[vis], box[vis, 0] // 16) and np.array_equal(tx1[vis], box[vis, 1] // 16)
     assert np.array_equal(ty0[vis], box[vis, 2] // 16) and np.array_equal(ty1[vis], box[vis, 3] // 16)
     cnt = r.arr("count", np.uint32, n)
