@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--scale-points", type=float, default=1.0, help="shrink the point count (tests)")
     ap.add_argument("--tile", type=int, default=0, help="tile edge: 16, 8, or 0 = autotuned with the blend depth")
     ap.add_argument("--blend-depth", type=int, default=0, help="records per blend batch (0 = tile^2)")
+    ap.add_argument("--record-copy", type=int, default=-1,
+                    help="training steps: 1 = the forward keeps the tile-ordered record copy for the backward, "
+                         "0 = not, -1 = autotuned with the split (on when --tile fixes the split)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bg", action="store_true", help="skip the background-model measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -146,11 +149,10 @@ def measured_peak_hbm():
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one
 # ncu capture of the kernel as it is built now, keyed by (kernel, workload id,
-# tile edge, blend depth). Random 32-byte record gathers and gradient-row
-# scatters move 64-byte DRAM bursts, hence traffic above the algorithmic bytes.
+# tile edge, blend depth, record copy). Random 32-byte record gathers and
+# gradient-row scatters move 64-byte DRAM bursts, hence traffic above the
+# algorithmic bytes. Empty until the captures of the current kernels are in.
 MEASURED_TRAFFIC = {
-    ("blend_bwd", 2, 8, 64): 711198464,
-    ("blend_fwd", 2, 8, 64): 323728128,
 }
 
 def kernel_bytes(name, w):
@@ -281,7 +283,7 @@ def run_ours(args, ws_, rank, local):
     gauss = scene.mode == "gaussian"
     # Training workloads keep the forward's tile-ordered record copy for the
     # backward (RAST_FLAG_SAVE_FOR_BWD); inference workloads do not need it.
-    flags = rast.FLAG_SAVE_FOR_BWD if scene.backward else 0
+    flags = rast.FLAG_SAVE_FOR_BWD if scene.backward and args.record_copy != 0 else 0
     opts = rast.make_opts(mode=scene.mode, tile=args.tile or 16, blend_depth=args.blend_depth, flags=flags)
     tens, cviews = make_views(scene, dev, bf16)
     tune = None
@@ -291,7 +293,8 @@ def run_ours(args, ws_, rank, local):
         from paper_2508_19140_gb300 import autotune
         tr = autotune.autotune(cviews, opts, rast.PASS_FWD | (rast.PASS_BWD if scene.backward else 0),
                                torch.cuda.current_stream(dev))
-        opts = autotune.with_split(opts, tr.tile, tr.blend_depth, tr.save_copy)
+        opts = autotune.with_split(opts, tr.tile, tr.blend_depth,
+                                   tr.save_copy if args.record_copy < 0 else None)
         tune = {"tile": tr.tile, "blend_depth": tr.blend_depth, "record_copy": tr.save_copy,
                 "from_cache": tr.from_cache,
                 "timings_ms": {autotune._label(c): (round(ms, 4) if ms is not None else None)
@@ -425,7 +428,8 @@ def run_ours(args, ws_, rank, local):
     if dom:
         k = kernels[dom]
         ach = k["gbs"] or 0.0
-        tkey = (dom, scene.config_id, int(opts.tile), int(opts.blend_depth) or int(opts.tile) ** 2)
+        copy = int(bool(int(opts.flags) & rast.FLAG_SAVE_FOR_BWD) and scene.mode == "bilinear")
+        tkey = (dom, scene.config_id, int(opts.tile), int(opts.blend_depth) or int(opts.tile) ** 2, copy)
         traffic = MEASURED_TRAFFIC.get(tkey) if args.scale_points == 1.0 else None
         roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": round(ach / peak, 4), "traffic": traffic,

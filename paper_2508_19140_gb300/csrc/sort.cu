@@ -171,9 +171,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
         }
     }
 
+    // The next tile is taken from the counter during the previous tile's last
+    // phase, so the loop spends no barrier on it. (A CTA holds the next tile
+    // only while finishing one it took earlier, which never waits on it: every
+    // look-back still ends.)
+    if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1u);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1u);
-        __syncthreads();
         const int64_t tile = *s_tile;
         if (tile >= ntiles) break;
         const int64_t base = tile * kSortTile;
@@ -253,6 +257,27 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
                 cuda::atomic_ref<uint32_t, cuda::thread_scope_device> w(my[bin]);
                 w.store((tile == 0 ? kFlagPrefix : kFlagAgg) | tot[q], cuda::memory_order_relaxed);
             }
+            if (bin < BINS) s_excl[bin] = tot[q];  // tile-local digit counts, scanned in place below
+        }
+        __syncthreads();
+        // Tile-local digit starts: warp 0 scans the BINS counts in place (each
+        // lane a run of consecutive bins) while the other warps look back.
+        if (warp == 0) {
+            constexpr int PER = BINS >= 32 ? BINS / 32 : 1;
+            uint32_t c[PER], sum = 0;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int bin = lane * PER + q;
+                c[q] = bin < BINS ? s_excl[bin] : 0u;
+                sum += c[q];
+            }
+            uint32_t run = warp_incl_scan(sum) - sum;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int bin = lane * PER + q;
+                if (bin < BINS) s_excl[bin] = run;
+                run += c[q];
+            }
         }
 #pragma unroll
         for (int q = 0; q < VPT; ++q) {
@@ -301,17 +326,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
             }
             s_gbase[bin] = s_goff[bin] + excl;
         }
-        uint32_t local = 0;
-#pragma unroll
-        for (int q = 0; q < VPT; ++q) local += tot[q];
-        uint32_t all;
-        uint32_t ex = block_excl_scan<kThreads>(local, s_warp, all);
-#pragma unroll
-        for (int q = 0; q < VPT; ++q) {
-            const int bin = threadIdx.x * VPT + q;
-            if (bin < BINS) s_excl[bin] = ex;
-            ex += tot[q];
-        }
         __syncthreads();
 
 #pragma unroll
@@ -335,6 +349,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
             if (kout) kout[dst] = key;
             vout[dst] = s_vals[j];
         }
+        if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1u);  // every thread has read this tile's index
         __syncthreads();
     }
 }
