@@ -265,10 +265,10 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
             const float w2 = __fmul_rn(ax, bg.b), w3 = __fmul_rn(bg.a, bg.b);
             s_w4[r] = make_float4(w0, w1, w2, w3);
             // 1 / (1 - alpha) of each slot, alpha = min(o w, amax) exactly as the forward has it
-            s_inv4[r] = make_float4(__frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w0), amax))),
-                                    __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w1), amax))),
-                                    __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w2), amax))),
-                                    __frcp_rn(__fsub_rn(1.f, fminf(__fmul_rn(o, w3), amax))));
+            s_inv4[r] = make_float4(rcp_fast(__fsub_rn(1.f, fminf(__fmul_rn(o, w0), amax))),
+                                    rcp_fast(__fsub_rn(1.f, fminf(__fmul_rn(o, w1), amax))),
+                                    rcp_fast(__fsub_rn(1.f, fminf(__fmul_rn(o, w2), amax))),
+                                    rcp_fast(__fsub_rn(1.f, fminf(__fmul_rn(o, w3), amax))));
             const int X0 = bg.i0 - tx * TS, Y0 = bg.j0 - ty * TS;
             anchor[k] = (X0 + 1) | ((Y0 + 1) << 8);
             s_azo[r] = make_uint4((uint32_t)anchor[k], g.z, g.w, 0u);
@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
                         const float o = ra.z;
                         const float og = __fmul_rn(o, G);
                         const float alpha = fminf(og, amax);
-                        const float inv = __frcp_rn(__fsub_rn(1.f, alpha));
+                        const float inv = rcp_fast(__fsub_rn(1.f, alpha));
                         const float Tk = T * inv;  // T_k = T_{k+1} / (1 - alpha_k)
                         float fr[C];
                         load_features<C, false>(reinterpret_cast<const uint32_t*>(s_f + r * C), fr);

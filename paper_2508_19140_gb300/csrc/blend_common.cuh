@@ -44,6 +44,17 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// 1 / x with the hardware reciprocal (rcp.approx: at most 1 ulp off, where an
+// IEEE-rounded reciprocal is a multi-instruction sequence). The backward's
+// replay T_k = T_{k+1} / (1 - alpha_k) uses it: 1 - alpha >= 1 - alpha_max
+// = 0.01, so x is never tiny, and each replay step then carries about 1.5 ulp
+// instead of 1 (the gradients' tolerance covers replays of thousands of steps).
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ---- TMA bulk copies completed on an mbarrier ---------------------------------
 // One thread arms the barrier with the batch's byte count and issues a single
 // global -> shared bulk copy of a contiguous run of records; every thread then

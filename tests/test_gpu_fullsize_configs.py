@@ -97,12 +97,16 @@ def test_gaussian_16m_bf16():
 
 
 def test_batched_8_views_bf16():
+    """At the split the benchmark runs for this workload: 8x8 tiles, blend
+    depth 64, and the forward's tile-ordered record copy that the backward
+    stages with TMA bulk copies."""
+    from paper_2508_19140_gb300 import rast
     scene = scenes.make_scene(5)
-    r = Run(scene.views, bf16=True, backward=True)
+    r = Run(scene.views, bf16=True, backward=True, tile=8, blend_depth=64, flags=rast.FLAG_SAVE_FOR_BWD)
     assert r.status == 0, r.stats
-    kw = _kw(scene)
+    kw = dict(mode=scene.mode, tile=8, pin32=True)
     keys, vals = r.sorted_copies()
-    offs = tile_offsets(scene.views)
+    offs = tile_offsets(scene.views, T=8)
     npt = np.cumsum([0] + [len(v.xyz) for v in scene.views])
     for k, v in enumerate(scene.views):
         sel = (keys >= offs[k]) & (keys < offs[k + 1])
