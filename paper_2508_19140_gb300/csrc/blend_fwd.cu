@@ -304,20 +304,28 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_bilinear(
     }
 }
 
-// Gaussian: each batch stages NT records as three 16-byte words (screen
-// position, opacity and depth; conic; pixel box) plus FP32 features, so a
-// lane reads a record with at most four broadcast shared-memory loads.
+// Gaussian: every warp owns an 8x4 sub-tile and walks the tile's list on its
+// own, 32 records at a time, with no CTA-wide barrier: each lane gathers one
+// record (the CTA's warps read the same records, so all but the first find
+// them in L1), stages it in the warp's own shared-memory rows as three
+// 16-byte words (screen position, opacity and depth; conic; pixel box) plus
+// FP32 features, and the warp ballots the records whose box meets its
+// sub-tile and composites those, all 32 lanes in lockstep. A warp stops as
+// soon as its own 32 pixels have terminated, and never waits for the other
+// sub-tiles of the tile. The next chunk's records are loaded while this one is
+// composited.
 template <int TS, int C, bool BF16>
 __global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pts, const uint32_t* __restrict__ rec, float* __restrict__ t_final,
     uint32_t* __restrict__ last_out, WsHeader* __restrict__ hdr) {
     constexpr int NT = TS * TS;
+    constexpr int NW = NT / 32;      // warps = 8x4 sub-tiles
     constexpr int WPR = TS / 8;      // warps per row of 8x4 sub-tiles
-    __shared__ float4 s_a[NT];       // (u - 1/2, v - 1/2, opacity, depth)
-    __shared__ float4 s_c[NT];       // conic (a, b, c), radius
-    __shared__ int4 s_box[NT];       // pixel box (x0, x1, y0, y1)
-    __shared__ __align__(16) float s_f[NT * C];
+    __shared__ float4 s_a[NW][32];   // (u - 1/2, v - 1/2, opacity, depth)
+    __shared__ float4 s_c[NW][32];   // conic (a, b, c), unused
+    __shared__ int4 s_box[NW][32];   // pixel box (x0, x1, y0, y1)
+    __shared__ __align__(16) float s_f[NW][32 * C];
     __shared__ uint32_t s_maxstop;
 
     const int64_t tile = order[blockIdx.x];
@@ -325,7 +333,6 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
     const int64_t lt = tile - V.tile_off;
     const int tx = (int)(lt % V.tiles_x), ty = (int)(lt / V.tiles_x);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // warp -> 8x4 sub-tile
     const int sx0 = tx * TS + (warp % WPR) * 8, sy0 = ty * TS + (warp / WPR) * 4;
     const int px = sx0 + (lane & 7), py = sy0 + (lane >> 3);
     const bool inside = px < V.W && py < V.H;
@@ -333,6 +340,10 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
     const int RW = vt.rec_words, FW = vt.feat_word;
     const float amax = vt.alpha_max, tmin = vt.t_min;
     const float fpx = (float)px, fpy = (float)py;
+    float4* const wa = s_a[warp];
+    float4* const wc = s_c[warp];
+    int4* const wbox = s_box[warp];
+    float* const wf = s_f[warp];
 
     float T = 1.f, A = 0.f, Dp = 0.f;
     float F[C];
@@ -346,84 +357,71 @@ __global__ void __launch_bounds__(TS * TS) k_blend_fwd_gauss(
     float f[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) f[c] = 0.f;
-    {
-        const uint32_t q = rg.x + tid;
-        if (q < rg.y) {
-            const uint32_t* rp = rec + (size_t)pts[q] * RW;
-            g = *reinterpret_cast<const uint4*>(rp);
-            h = *reinterpret_cast<const uint4*>(rp + 4);
-            load_features<C, BF16>(rp + FW, f);
-        }
+    if (rg.x + lane < rg.y) {
+        const uint32_t* rp = rec + (size_t)pts[rg.x + lane] * RW;
+        g = *reinterpret_cast<const uint4*>(rp);
+        h = *reinterpret_cast<const uint4*>(rp + 4);
+        load_features<C, BF16>(rp + FW, f);
     }
-    uint32_t gi_next = (rg.x + NT + tid < rg.y) ? pts[rg.x + NT + tid] : 0u;
-    __syncthreads();
+    uint32_t gi_next = (rg.x + 32 + lane < rg.y) ? pts[rg.x + 32 + lane] : 0u;
 
-    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += NT) {
-        if (b0 + tid < rg.y) {
+#pragma unroll 1
+    for (uint32_t q0 = rg.x; q0 < rg.y; q0 += 32) {
+        if (__all_sync(0xffffffffu, done)) break;  // this sub-tile is finished
+        bool hit = false;
+        if (q0 + lane < rg.y) {
             const float um = __fsub_rn(__uint_as_float(g.x), 0.5f);
             const float vm = __fsub_rn(__uint_as_float(g.y), 0.5f);
             const GaussBox bx = gauss_box(um, vm, __uint_as_float(h.w));
-            s_a[tid] = make_float4(um, vm, __uint_as_float(g.w), __uint_as_float(g.z));
-            s_c[tid] = make_float4(__uint_as_float(h.x), __uint_as_float(h.y), __uint_as_float(h.z), 0.f);
-            s_box[tid] = make_int4(bx.x0, bx.x1, bx.y0, bx.y1);
-            store_row<C>(s_f + tid * C, f);
+            wa[lane] = make_float4(um, vm, __uint_as_float(g.w), __uint_as_float(g.z));
+            wc[lane] = make_float4(__uint_as_float(h.x), __uint_as_float(h.y), __uint_as_float(h.z), 0.f);
+            wbox[lane] = make_int4(bx.x0, bx.x1, bx.y0, bx.y1);
+            store_row<C>(wf + lane * C, f);
+            hit = bx.x0 <= sx0 + 7 && bx.x1 >= sx0 && bx.y0 <= sy0 + 3 && bx.y1 >= sy0;
         }
-        if (__syncthreads_count(!done) == 0) break;
+        uint32_t m = __ballot_sync(0xffffffffu, hit);
+        __syncwarp();
         {
-            const uint32_t qn = b0 + NT + tid;
+            // the next chunk's record (and the point index of the one after)
+            const uint32_t qn = q0 + 32 + lane;
             if (qn < rg.y) {
                 const uint32_t* rp = rec + (size_t)gi_next * RW;
                 g = *reinterpret_cast<const uint4*>(rp);
                 h = *reinterpret_cast<const uint4*>(rp + 4);
                 load_features<C, BF16>(rp + FW, f);
             }
-            gi_next = (qn + NT < rg.y) ? pts[qn + NT] : 0u;
+            gi_next = (qn + 32 < rg.y) ? pts[qn + 32] : 0u;
         }
-        const int nrec = (int)min((uint32_t)NT, rg.y - b0);
-        const uint32_t rel0 = b0 - rg.x;
-        if (!__all_sync(0xffffffffu, done)) {
-#pragma unroll 1
-            for (int grp = 0; grp < NT / 32; ++grp) {
-                const int r0 = grp * 32;
-                if (r0 >= nrec) break;
-                bool hit = false;
-                if (r0 + lane < nrec) {
-                    const int4 bb = s_box[r0 + lane];
-                    hit = bb.x <= sx0 + 7 && bb.y >= sx0 && bb.z <= sy0 + 3 && bb.w >= sy0;
-                }
-                uint32_t m = __ballot_sync(0xffffffffu, hit);
-                while (m) {
-                    const int r = r0 + __ffs(m) - 1;
-                    m &= m - 1;
-                    if (done) continue;
-                    const int4 bb = s_box[r];
-                    if (px < bb.x || px > bb.y || py < bb.z || py > bb.w) continue;
-                    const float4 ra = s_a[r];
-                    const float4 rc = s_c[r];
-                    const float dx = __fsub_rn(fpx, ra.x), dy = __fsub_rn(fpy, ra.y);
-                    const float mm = gauss_m(dx, dy, rc.x, rc.y, rc.z);
-                    if (!(mm <= 9.f)) continue;
-                    const float alpha = fminf(__fmul_rn(ra.z, gauss_value(mm)), amax);
-                    const float nT = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                    if (nT < tmin) {
-                        done = true;
-                        stop = rel0 + r + 1;
-                        continue;
-                    }
-                    float fr[C];
-                    load_features<C, false>(reinterpret_cast<const uint32_t*>(s_f + r * C), fr);
-                    const float ta = T * alpha;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) F[c] = fmaf(ta, fr[c], F[c]);
-                    Dp = fmaf(ta, ra.w, Dp);
-                    A += ta;
-                    T = nT;
-                    last = rel0 + r + 1;
-                }
-                if (__all_sync(0xffffffffu, done)) break;
+        const uint32_t rel0 = q0 - rg.x;
+        while (m) {
+            const int r = __ffs(m) - 1;
+            m &= m - 1;
+            if (done) continue;
+            const int4 bb = wbox[r];
+            if (px < bb.x || px > bb.y || py < bb.z || py > bb.w) continue;
+            const float4 ra = wa[r];
+            const float4 rc = wc[r];
+            const float dx = __fsub_rn(fpx, ra.x), dy = __fsub_rn(fpy, ra.y);
+            const float mm = gauss_m(dx, dy, rc.x, rc.y, rc.z);
+            if (!(mm <= 9.f)) continue;
+            const float alpha = fminf(__fmul_rn(ra.z, gauss_value(mm)), amax);
+            const float nT = __fmul_rn(T, __fsub_rn(1.f, alpha));
+            if (nT < tmin) {
+                done = true;
+                stop = rel0 + r + 1;
+                continue;
             }
+            float fr[C];
+            load_features<C, false>(reinterpret_cast<const uint32_t*>(wf + r * C), fr);
+            const float ta = T * alpha;
+#pragma unroll
+            for (int c = 0; c < C; ++c) F[c] = fmaf(ta, fr[c], F[c]);
+            Dp = fmaf(ta, ra.w, Dp);
+            A += ta;
+            T = nT;
+            last = rel0 + r + 1;
         }
-        __syncthreads();
+        __syncwarp();  // the warp's rows are refilled by the next chunk
     }
 
     if (inside) {
