@@ -123,12 +123,24 @@ __global__ void __launch_bounds__(kT) k_dup_count(const uint32_t* __restrict__ s
     if (threadIdx.x == 0) blk[blockIdx.x] = tot;
 }
 
+// Per-point copy counts, kPer consecutive points from s0: the count array
+// (Gaussian), or the packed bilinear rects (P4; an empty rect counts 0).
+template <bool P4>
+__device__ __forceinline__ void load_counts(const uint32_t* __restrict__ p, int64_t s0, int64_t n, uint32_t v[kPer]) {
+    load_u32s(p, s0, n, v, P4 ? kRect4Empty : 0u);
+    if constexpr (P4) {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) v[j] = rect4_count(v[j]);
+    }
+}
+
+template <bool P4>
 __global__ void __launch_bounds__(kT) k_count_blocks(const uint32_t* __restrict__ cnt, int64_t n,
                                                      uint32_t* __restrict__ blk) {
     __shared__ uint32_t s_warp[33];
     const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
     uint32_t v[kPer];
-    load_u32s(cnt, s0, n, v, 0u);
+    load_counts<P4>(cnt, s0, n, v);
     uint32_t sum = 0;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) sum += v[j];
@@ -239,13 +251,14 @@ __global__ void __launch_bounds__(kTW) k_dup_write(const ViewTable vt, const uin
     }
 }
 
+template <bool P4>
 __global__ void __launch_bounds__(kT) k_scan_apply(const uint32_t* __restrict__ cnt, int64_t n,
                                                    const uint32_t* __restrict__ blk,
                                                    uint32_t* __restrict__ base) {
     __shared__ uint32_t s_warp[33];
     const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPer;
     uint32_t v[kPer];
-    load_u32s(cnt, s0, n, v, 0u);
+    load_counts<P4>(cnt, s0, n, v);
     uint32_t sum = 0;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) sum += v[j];
@@ -358,12 +371,12 @@ cudaError_t launch_untiled_copies(const ViewTable& vt, const Bufs& b, const uint
     if (nb == 0) return cudaSuccess;
     {
         ProfScope ps("dup.count", s);
-        k_count_blocks<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk);
+        k_count_blocks<true><<<(unsigned)nb, kT, 0, s>>>(b.rect4, n, b.blk);
     }
     {
         ProfScope ps("dup.scan", s);
         k_scan_blocks<<<1, 1024, 0, s>>>(b.blk, nb, b.hdr, b.copy_cap);
-        k_scan_apply<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk, b.base);
+        k_scan_apply<true><<<(unsigned)nb, kT, 0, s>>>(b.rect4, n, b.blk, b.base);
     }
     {
         ProfScope ps("dup.write", s);
@@ -428,7 +441,8 @@ cudaError_t launch_point_scan(const ViewTable& vt, const Bufs& b, cudaStream_t s
     if (nb == 0) return cudaSuccess;
     {
         ProfScope ps("point_scan.count", s);
-        k_count_blocks<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk);
+        if (vt.mode == 0) k_count_blocks<true><<<(unsigned)nb, kT, 0, s>>>(b.rect4, n, b.blk);
+        else k_count_blocks<false><<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk);
     }
     {
         ProfScope ps("point_scan.scan", s);
@@ -436,7 +450,8 @@ cudaError_t launch_point_scan(const ViewTable& vt, const Bufs& b, cudaStream_t s
     }
     {
         ProfScope ps("point_scan.apply", s);
-        k_scan_apply<<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk, b.base);
+        if (vt.mode == 0) k_scan_apply<true><<<(unsigned)nb, kT, 0, s>>>(b.rect4, n, b.blk, b.base);
+        else k_scan_apply<false><<<(unsigned)nb, kT, 0, s>>>(b.cnt, n, b.blk, b.base);
     }
     return cudaGetLastError();
 }

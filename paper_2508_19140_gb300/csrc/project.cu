@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs 
                           : kRect4Empty;
     else
         b.rect[gi] = rect;
-    b.cnt[gi] = count;
+    if (MODE == 1) b.cnt[gi] = count;  // bilinear counts come from the packed rect (rect4_count)
     b.zbits[gi] = __float_as_uint(zc);
 }
 

@@ -221,7 +221,7 @@ struct Bufs {
     uint32_t* rec_tile;   // bilinear: the records the forward blend read, in tile-list order (per copy)
     uint2* rect;          // tile rect per point (Gaussian; bilinear: rect4)
     uint32_t* rect4;      // bilinear: packed tile rect per point (same memory as rect)
-    uint32_t* cnt;        // copies per point (point order)
+    uint32_t* cnt;        // copies per point (point order; Gaussian only: bilinear counts come from rect4)
     uint32_t* zbits;      // FP32 bits of the view depth per point (backward bookkeeping)
     uint32_t* keyA[2];    // depth sort ping-pong
     uint32_t* valA[2];
