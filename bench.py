@@ -151,8 +151,17 @@ def measured_peak_hbm():
 # ncu capture of the kernel as it is built now, keyed by (kernel, workload id,
 # tile edge, blend depth, record copy). Random 32-byte record gathers and
 # gradient-row scatters move 64-byte DRAM bursts, hence traffic above the
-# algorithmic bytes. Empty until the captures of the current kernels are in.
+# algorithmic bytes (profiles/ncu_blend_traffic_all_workloads.md).
 MEASURED_TRAFFIC = {
+    ("blend_fwd", 2, 8, 64, 0): 324530432,
+    ("blend_bwd", 2, 8, 64, 0): 707129600,
+    ("blend_fwd", 2, 8, 64, 1): 528297216,
+    ("blend_bwd", 2, 8, 64, 1): 412425216,
+    ("blend_fwd", 3, 16, 256, 0): 2890925056,
+    ("blend_fwd", 4, 16, 256, 0): 382870272,
+    ("blend_bwd", 4, 16, 256, 0): 1125356032,
+    ("blend_fwd", 5, 8, 64, 1): 9635505408,
+    ("blend_bwd", 5, 8, 64, 1): 9302492928,
 }
 
 def kernel_bytes(name, w):
