@@ -20,15 +20,54 @@
 namespace rast {
 namespace {
 
-template <int MODE>
-__global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs b, bool write_vals) {
-    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= vt.n_total) return;
-    const int vi = view_of_point(vt, gi);
-    const ViewDev& V = vt.v[vi];
-    const int64_t i = gi - V.pt_off;
+// Inputs of one point, loaded before any of the block's points is computed.
+struct PointIn {
+    float x, y, z, o, s;
+    uint4 f[2];      // the features' raw words when they fit in 32 aligned bytes
+    int nf;          // feature words in f as 16-byte vectors: 1 or 2; -1 = one 8-byte pair
+                     // (BF16, C = 4); 0 = not loaded (the body copies the features itself)
+};
 
-    const float x = V.xyz[3 * i + 0], y = V.xyz[3 * i + 1], z = V.xyz[3 * i + 2];
+// Loads a point's inputs (features as raw words on the aligned paths: FP32 with
+// C a multiple of 4 up to 8, BF16 with C 4, 8 or 16).
+template <int MODE>
+__device__ __forceinline__ void load_point(const ViewTable& vt, const ViewDev& V, int64_t i, PointIn& in) {
+    in.x = V.xyz[3 * i + 0];
+    in.y = V.xyz[3 * i + 1];
+    in.z = V.xyz[3 * i + 2];
+    in.o = V.opacity[i];
+    in.s = 0.f;
+    if (MODE == 1) in.s = V.scale ? V.scale[i] : __fdiv_rn(__fmul_rn(5.f, V.near_z), V.fx);
+    in.nf = 0;
+    const int C = vt.C;
+    if (!vt.bf16) {
+        // FP32: C = 4 is one 16-byte vector, C = 8 two.
+        const float* f = static_cast<const float*>(V.feat) + i * C;
+        if ((C == 4 || C == 8) && (reinterpret_cast<uintptr_t>(f) & 15) == 0) {
+            in.f[0] = *reinterpret_cast<const uint4*>(f);
+            if (C == 8) in.f[1] = *reinterpret_cast<const uint4*>(f + 4);
+            in.nf = C / 4;
+        }
+    } else {
+        // BF16: C = 8 is one 16-byte vector, C = 16 two, C = 4 one 8-byte pair.
+        const unsigned short* f = static_cast<const unsigned short*>(V.feat) + i * C;
+        const uintptr_t fa = reinterpret_cast<uintptr_t>(f);
+        if ((C == 8 || C == 16) && (fa & 15) == 0) {
+            in.f[0] = *reinterpret_cast<const uint4*>(f);
+            if (C == 16) in.f[1] = *reinterpret_cast<const uint4*>(f + 8);
+            in.nf = C / 8;
+        } else if (C == 4 && (fa & 7) == 0) {
+            const uint2 q = *reinterpret_cast<const uint2*>(f);
+            in.f[0] = make_uint4(q.x, q.y, 0u, 0u);
+            in.nf = -1;
+        }
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void project_point(const ViewTable& vt, const Bufs& b, bool write_vals, int64_t gi,
+                                              const ViewDev& V, int64_t i, const PointIn& in) {
+    const float x = in.x, y = in.y, z = in.z;
     float xc = __fmul_rn(V.R[0], x);
     xc = __fadd_rn(xc, __fmul_rn(V.R[1], y));
     xc = __fadd_rn(xc, __fmul_rn(V.R[2], z));
@@ -61,7 +100,7 @@ __global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs 
                 by1 = min(j0 + 1, V.H - 1);
             }
         } else {
-            const float s = V.scale ? V.scale[i] : __fdiv_rn(__fmul_rn(5.f, V.near_z), V.fx);
+            const float s = in.s;
             const float s2 = __fmul_rn(s, s);
             const float zz = __fmul_rn(zc, zc);
             float S00, S01, S11;
@@ -115,7 +154,7 @@ __global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs 
 
         // Record: u, v, z, o [, a, b, c, r], features.
         uint32_t* rec = b.rec + gi * vt.rec_words;
-        const float o = V.opacity[i];
+        const float o = in.o;
         *reinterpret_cast<uint4*>(rec) =
             make_uint4(__float_as_uint(u), __float_as_uint(v), __float_as_uint(zc), __float_as_uint(o));
         if (MODE == 1)
@@ -123,7 +162,15 @@ __global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs 
                                                             __float_as_uint(cc), __float_as_uint(r));
         uint32_t* fw = rec + vt.feat_word;
         const int C = vt.C;
-        if (!vt.bf16) {
+        if (in.nf != 0) {
+            // exactly the feature words of the record: 8 bytes, or 16 / 32 bytes
+            if (in.nf < 0) {
+                *reinterpret_cast<uint2*>(fw) = make_uint2(in.f[0].x, in.f[0].y);
+            } else {
+                *reinterpret_cast<uint4*>(fw) = in.f[0];
+                if (in.nf == 2) *reinterpret_cast<uint4*>(fw + 4) = in.f[1];
+            }
+        } else if (!vt.bf16) {
             const float* f = static_cast<const float*>(V.feat) + i * C;
             if ((C & 3) == 0 && ((reinterpret_cast<uintptr_t>(f) & 15) == 0)) {
                 for (int c = 0; c < C; c += 4)
@@ -161,11 +208,42 @@ __global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs 
     b.zbits[gi] = __float_as_uint(zc);
 }
 
+// kPointsPerThread points per thread, all their loads issued before any is
+// computed: the kernel waits on one memory round trip per thread instead of
+// two per point (inputs, then features).
+constexpr int kPointsPerThread = 2;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_project(const ViewTable vt, const Bufs b, bool write_vals) {
+    constexpr int K = kPointsPerThread;
+    const int64_t g0 = (int64_t)blockIdx.x * (256 * K) + threadIdx.x;
+    PointIn in[K];
+    int vi[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t gi = g0 + k * 256;
+        vi[k] = 0;
+        if (gi < vt.n_total) {
+            vi[k] = view_of_point(vt, gi);
+            const ViewDev& V = vt.v[vi[k]];
+            load_point<MODE>(vt, V, gi - V.pt_off, in[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t gi = g0 + k * 256;
+        if (gi < vt.n_total) {
+            const ViewDev& V = vt.v[vi[k]];
+            project_point<MODE>(vt, b, write_vals, gi, V, gi - V.pt_off, in[k]);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_project(const ViewTable& vt, const Bufs& b, bool write_vals, cudaStream_t s) {
     if (vt.n_total == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)((vt.n_total + 255) / 256);
+    const unsigned grid = (unsigned)((vt.n_total + 256 * kPointsPerThread - 1) / (256 * kPointsPerThread));
     ProfScope ps("project", s);
     if (vt.mode == 0) k_project<0><<<grid, 256, 0, s>>>(vt, b, write_vals);
     else k_project<1><<<grid, 256, 0, s>>>(vt, b, write_vals);
