@@ -421,12 +421,13 @@ __global__ void __launch_bounds__(TS * TS, TS == 8 && RPT == 1 ? 16 : 1) k_blend
 // ---------------------------------------------------------------- Gaussian
 
 // Warp sums of N values per lane by recursive halving: at each level a lane
-// keeps one half of its values and adds the partner lane's copy of that half,
-// so N values cost N/2 + N/4 + ... + 1 shuffles (plus the full butterfly over
-// the offsets left once one value remains) instead of five per value. Lane
-// (32 / N) * k returns the sum of value k. Each sum is formed over the same
-// pairing tree as an xor butterfly over offsets 16, 8, 4, 2, 1, so the bits do
-// not depend on which lane holds it or on timing.
+// keeps one half of its values (the upper half, ceil(N/2) slots with the
+// missing ones zero, on lanes with the level's offset bit set) and adds the
+// partner lane's copy of that half, so N values cost about N shuffles in all
+// instead of five per value; scatter_index() says which value a lane ends up
+// holding. Each sum is formed over the same pairing tree as an xor butterfly
+// over offsets 16, 8, 4, 2, 1, so its bits do not depend on which lane holds
+// it, on timing, or on how the values are split into halves.
 template <int N, int OFF>
 __device__ __forceinline__ float warp_reduce_scatter(const float (&v)[N], int lane) {
     if constexpr (N == 1) {
@@ -435,34 +436,86 @@ __device__ __forceinline__ float warp_reduce_scatter(const float (&v)[N], int la
         for (int o = OFF; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         return x;
     } else {
-        float w[N / 2];
+        static_assert(OFF > 0, "at most 32 values");
+        constexpr int H = (N + 1) / 2;
+        float w[H];
         const bool up = (lane & OFF) != 0;
 #pragma unroll
-        for (int k = 0; k < N / 2; ++k) {
-            const float lo = v[k], hi = v[k + N / 2];
+        for (int k = 0; k < H; ++k) {
+            const float lo = v[k], hi = k + H < N ? v[k + H] : 0.f;
             w[k] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, OFF);
         }
-        return warp_reduce_scatter<N / 2, OFF / 2>(w, lane);
+        return warp_reduce_scatter<H, OFF / 2>(w, lane);
     }
 }
 
-// Gaussian backward batch: records per batch and the padded contribution row.
-template <int TS>
-__host__ __device__ constexpr int gauss_bwd_batch() { return TS * TS >= 256 ? 128 : TS * TS; }
-__host__ __device__ constexpr int gauss_contrib_stride(int P) { return P | 1; }  // odd: conflict-free rows
-template <int TS, int C>
-constexpr size_t gauss_bwd_smem() {
-    return sizeof(float) * (TS * TS / 32) * gauss_bwd_batch<TS>() * gauss_contrib_stride(C + 7);
+// The value whose sum warp_reduce_scatter<N, OFF> returns on `lane`, or -1 if
+// the lane holds a padding slot or a copy that a lower lane also holds.
+template <int N, int OFF>
+__device__ __forceinline__ int scatter_index(int lane) {
+    if constexpr (N == 1) {
+        return OFF == 0 || (lane & (2 * OFF - 1)) == 0 ? 0 : -1;
+    } else {
+        constexpr int H = (N + 1) / 2;
+        const int sub = scatter_index<H, OFF / 2>(lane);
+        if (sub < 0) return -1;
+        const int idx = ((lane & OFF) ? H : 0) + sub;
+        return idx < N ? idx : -1;
+    }
 }
 
-// Per batch of GB records: every warp (an 8x4 sub-tile) ballots the records
-// whose pixel box meets its sub-tile; for each such record that some lane
+// Gaussian backward: records per batch, batches in flight, padded rows.
+constexpr int kGaussBatch = 32;   // records per batch: one ballot per warp and batch
+constexpr int kGaussStages = 4;   // batches staged at once (how far warps may drift apart)
+__host__ __device__ constexpr int gauss_contrib_stride(int P) { return P | 1; }  // odd: conflict-free rows
+// Staged words of a record: the used prefix (u, v, z, o, conic, radius,
+// features) rounded to 16 bytes. A stride of 12 words keeps the lane-parallel
+// reads of the ballot step free of bank conflicts.
+template <int C, bool BF16>
+__host__ __device__ constexpr int gauss_ring_stride() {
+    return (RecLayout<1, C, BF16>::need + 3) & ~3;
+}
+template <int TS, int C, bool BF16>
+constexpr size_t gauss_bwd_smem() {
+    return 128 + sizeof(uint32_t) * kGaussStages * kGaussBatch * gauss_ring_stride<C, BF16>() +
+           sizeof(float) * kGaussStages * (TS * TS / 32) * kGaussBatch * gauss_contrib_stride(C + 7);
+}
+
+// Polls `bar` for the phase of this parity, giving up after kMbarPolls polls
+// or once another warp of the CTA has given up (abort flag).
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const volatile uint32_t* abort) {
+    const uint32_t b = smem_addr(bar);
+    for (uint32_t i = 0; i < kMbarPolls; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 63u) == 63u && *abort) return false;
+    }
+    return false;
+}
+
+// The warps of a tile (8x4 sub-tiles) run through the tile's batches without
+// CTA barriers. A batch of kGaussBatch records sits in one of kGaussStages
+// ring stages; one warp stages it with per-lane cp.async copies (record, point
+// index, partial-slot base) that complete on the stage's mbarrier, and every
+// warp waits on that barrier's phases in order. Per batch a warp ballots the
+// records whose pixel box meets its sub-tile; for each one that some lane
 // really blended (inside its box, m <= 9, before the pixel's last fragment)
 // the lanes compute their P contributions, sum them over the warp with one
-// reduce-scatter, and the lanes holding the sums write the record's row of the
-// warp's contribution table (rows of odd stride: conflict-free) and a hit bit.
-// After a barrier each record's loader thread adds the rows of the warps that
-// hit it, in warp order, and writes the copy's partial row.
+// reduce-scatter, and the lanes holding the sums write the record's row of
+// the warp's contribution table (rows of odd stride: conflict-free) and a hit
+// bit. The warp then counts itself done with the batch; the last of the NW
+// warps adds the rows of the warps that hit each record, in warp order (the
+// sum does not depend on which warp comes last), writes the copies' partial
+// rows, clears the stage and stages the batch kGaussStages further on. Warps
+// may thus drift apart by up to kGaussStages - 1 batches: a tile costs about
+// its slowest warp's work, not the sum over batches of each batch's slowest.
 template <int TS, int C, bool BF16>
 __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     const ViewTable vt, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
@@ -473,19 +526,26 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     constexpr int NT = TS * TS;
     constexpr int NW = NT / 32;                    // warps = 8x4 sub-tiles
     constexpr int WPR = TS / 8;                    // sub-tiles per row
-    constexpr int GB = gauss_bwd_batch<TS>();      // records per backward batch
+    constexpr int GB = kGaussBatch;
+    constexpr int R = kGaussStages;
     constexpr int NG = GB / 32;                    // ballot groups per batch
     constexpr int P = C + 7;  // dfeat[C], do, du, dv, dca, dcb, dcc, dz
-    constexpr int PP = P <= 8 ? 8 : (P <= 16 ? 16 : 32);
-    constexpr int LPV = 32 / PP;                   // lanes holding each warp sum
     constexpr int PO = gauss_contrib_stride(P);
-    __shared__ float4 s_a[GB];                     // (u - 1/2, v - 1/2, opacity, depth)
-    __shared__ float4 s_c[GB];                     // conic (a, b, c), radius
-    __shared__ int4 s_box[GB];                     // pixel box (x0, x1, y0, y1)
-    __shared__ __align__(16) float s_f[GB * C];    // FP32 features
-    __shared__ uint32_t s_hit[NW * NG];            // records each warp contributed to
-    extern __shared__ float s_contrib[];           // [NW][GB][PO]
+    constexpr int PS = partial_stride(P);
+    constexpr int RW = RecLayout<1, C, BF16>::words;
+    constexpr int RS = gauss_ring_stride<C, BF16>();
+    constexpr int FW = RecLayout<1, C, BF16>::feat_word;
+    extern __shared__ __align__(128) uint32_t s_dyn[];
+    uint32_t* const s_ring = align128(s_dyn);                                     // [R][GB][RS]
+    float* const s_contrib = reinterpret_cast<float*>(s_ring + R * GB * RS);      // [R][NW][GB][PO]
+    __shared__ uint32_t s_gi[R][GB];               // point index of each staged record
+    __shared__ uint32_t s_base[R][GB];             // its first partial slot
+    __shared__ uint32_t s_hit[R][NW * NG];         // records each warp contributed to
+    __shared__ uint32_t s_done[R];                 // warps done with the stage's batch
+    __shared__ __align__(8) uint64_t s_mbar[R];    // stage filled (32 arrivals: the staging lanes)
+    __shared__ int4 s_box[NW][GB];                 // per warp: pixel boxes of the batch's records
     __shared__ uint32_t s_red;
+    __shared__ uint32_t s_abort;
 
     const int64_t tile = order[blockIdx.x];
     const ViewDev& V = vt.v[view_of_tile(vt, tile)];
@@ -496,7 +556,6 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     const int px = sx0 + (lane & 7), py = sy0 + (lane >> 3);
     const bool inside = px < V.W && py < V.H;
     const uint2 rg = ranges[tile];
-    const int RW = vt.rec_words, FW = vt.feat_word;
     const float amax = vt.alpha_max;
     const float fpx = (float)px, fpy = (float)py;
 
@@ -514,6 +573,16 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
         if (V.g_alpha) gA = V.g_alpha[pix];
         if (V.g_depth) gD = V.g_depth[pix];
     }
+    if (tid < R) s_done[tid] = 0;
+    for (int i = tid; i < R * NW * NG; i += NT) (&s_hit[0][0])[i] = 0;
+    if (tid == 0) {
+        s_abort = 0;
+#pragma unroll
+        for (int st = 0; st < R; ++st) mbar_init(&s_mbar[st], 32);
+        mbar_init_fence();
+    }
+    // The barriers inside block_max_u32 also order the initialisation above
+    // before any copy or wait.
     const uint32_t maxlast = block_max_u32(last, &s_red);
     if (tid == 0 && maxlast) atomicAdd(&hdr->needed_bwd, (unsigned long long)maxlast);
     if (maxlast == 0) {
@@ -523,150 +592,178 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     float Sg = 0.f, SD = 0.f;
     const float Kd = -gA * Tfin;
     const uint32_t end = rg.x + maxlast;
-    const int nb = (int)((maxlast - 1) / GB);
-    const bool loader = tid < GB;
+    const uint32_t nb = (maxlast - 1) / GB + 1;  // batches; iteration j handles batch nb - 1 - j
     const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
+    const int my_k = scatter_index<P, 16>(lane);  // the warp sum this lane writes, if any
 
-    uint4 g = make_uint4(0u, 0u, 0u, 0u), h = make_uint4(0u, 0u, 0u, 0u);
-    float f[C];
+    // Stages iteration j (all 32 lanes of one warp): lane l copies record l of
+    // the batch, its point index and its partial-slot base, then arrives on
+    // the stage's barrier once its copies have landed.
+    auto stage = [&](uint32_t j) {
+        const int st = (int)(j % R);
 #pragma unroll
-    for (int c = 0; c < C; ++c) f[c] = 0.f;
-    uint32_t gi = 0, bs = 0;
-    if (loader) {
-        const uint32_t q = rg.x + (uint32_t)nb * GB + tid;
-        if (q < end) {
-            gi = pts[q];
-            const uint32_t* rp = rec + (size_t)gi * RW;
-            g = *reinterpret_cast<const uint4*>(rp);
-            h = *reinterpret_cast<const uint4*>(rp + 4);
-            load_features<C, BF16>(rp + FW, f);
-            bs = base[gi];
-        }
-    }
-    uint32_t gi_next = (loader && nb > 0) ? pts[rg.x + (uint32_t)(nb - 1) * GB + tid] : 0u;
-
-    for (int bi = nb; bi >= 0; --bi) {
-        const uint32_t rel0 = (uint32_t)bi * GB;
-        const uint32_t b0 = rg.x + rel0;
-        const uint32_t bend = end < b0 + GB ? end : b0 + GB;
-        const int nrec = (int)(bend - b0);
-        if (tid < NW * NG) s_hit[tid] = 0u;
-        const bool have = loader && b0 + tid < bend;
-        const uint32_t my_bs = bs;
-        int slot = 0;
-        if (have) {
-            const float um = __fsub_rn(__uint_as_float(g.x), 0.5f);
-            const float vm = __fsub_rn(__uint_as_float(g.y), 0.5f);
-            const GaussBox bx = gauss_box(um, vm, __uint_as_float(h.w));
-            s_a[tid] = make_float4(um, vm, __uint_as_float(g.w), __uint_as_float(g.z));
-            s_c[tid] = make_float4(__uint_as_float(h.x), __uint_as_float(h.y), __uint_as_float(h.z), 0.f);
-            s_box[tid] = make_int4(bx.x0, bx.x1, bx.y0, bx.y1);
-            store_row<C>(s_f + tid * C, f);
-            // tile rect of the in-image box, as the projection computed it
-            const int tx0 = max(bx.x0, 0) / TS, tx1 = min(bx.x1, V.W - 1) / TS;
-            const int ty0 = max(bx.y0, 0) / TS;
-            slot = (ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0);
-            if (b0 + tid + 1 == end) cutoff[tile] = make_uint2(g.z, gi);
-        }
-        __syncthreads();
-        if (loader && bi > 0) {
-            gi = gi_next;
-            const uint32_t* rp = rec + (size_t)gi * RW;
-            g = *reinterpret_cast<const uint4*>(rp);
-            h = *reinterpret_cast<const uint4*>(rp + 4);
-            load_features<C, BF16>(rp + FW, f);
-            bs = base[gi];
-            gi_next = (bi > 1) ? pts[b0 - 2 * GB + tid] : 0u;
-        }
-        if (wlast > rel0) {
-#pragma unroll 1
-            for (int grp = (nrec - 1) / 32; grp >= 0; --grp) {
-                const int r0 = grp * 32;
-                bool hit = false;
-                if (r0 + lane < nrec) {
-                    const int4 bb = s_box[r0 + lane];
-                    hit = bb.x <= sx0 + 7 && bb.y >= sx0 && bb.z <= sy0 + 3 && bb.w >= sy0;
-                }
-                uint32_t m = __ballot_sync(0xffffffffu, hit);
-                uint32_t written = 0;
-                while (m) {
-                    const int bit = 31 - __clz(m);
-                    m &= ~(1u << bit);
-                    const int r = r0 + bit;
-                    const int4 bb = s_box[r];
-                    bool act = inside && rel0 + r < last && px >= bb.x && px <= bb.y && py >= bb.z && py <= bb.w;
-                    float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rc = ra;
-                    float dx = 0.f, dy = 0.f, mm = 0.f;
-                    if (act) {
-                        ra = s_a[r];
-                        rc = s_c[r];
-                        dx = __fsub_rn(fpx, ra.x);
-                        dy = __fsub_rn(fpy, ra.y);
-                        mm = gauss_m(dx, dy, rc.x, rc.y, rc.z);
-                        act = mm <= 9.f;
-                    }
-                    if (!__any_sync(0xffffffffu, act)) continue;  // no lane blended this record
-                    written |= 1u << bit;
-                    float v[PP];
+        for (int g = 0; g < NG; ++g) {
+            const int rr = g * 32 + lane;
+            const uint32_t q = rg.x + (nb - 1 - j) * GB + rr;
+            if (q < end) {
+                const uint32_t gi = pts[q];
+                uint32_t* dst = s_ring + ((size_t)st * GB + rr) * RS;
+                const uint32_t* src = rec + (size_t)gi * RW;
 #pragma unroll
-                    for (int k = 0; k < PP; ++k) v[k] = 0.f;
-                    if (act) {
-                        const float G = gauss_value(mm);
-                        const float o = ra.z;
-                        const float og = __fmul_rn(o, G);
-                        const float alpha = fminf(og, amax);
-                        const float inv = rcp_fast(__fsub_rn(1.f, alpha));
-                        const float Tk = T * inv;  // T_k = T_{k+1} / (1 - alpha_k)
-                        float fr[C];
-                        load_features<C, false>(reinterpret_cast<const uint32_t*>(s_f + r * C), fr);
-                        float fdot = 0.f;
-#pragma unroll
-                        for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], fr[c], fdot);
-                        const float z = ra.w;
-                        const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) * inv;
-                        const float ta = Tk * alpha;
-                        Sg = fmaf(ta, fdot, Sg);
-                        SD = fmaf(ta, z, SD);
-                        T = Tk;
-#pragma unroll
-                        for (int c = 0; c < C; ++c) v[c] = ta * gF[c];
-                        v[C + 6] = ta * gD;
-                        if (og <= amax) {
-                            const float dm = -0.5f * o * G * dalpha;
-                            v[C] = G * dalpha;
-                            v[C + 1] = -dm * (2.f * rc.x * dx + 2.f * rc.y * dy);
-                            v[C + 2] = -dm * (2.f * rc.y * dx + 2.f * rc.z * dy);
-                            v[C + 3] = dm * dx * dx;
-                            v[C + 4] = dm * 2.f * dx * dy;
-                            v[C + 5] = dm * dy * dy;
-                        }
-                    }
-                    const float sum = warp_reduce_scatter<PP, 16>(v, lane);
-                    const int k = lane / LPV;
-                    if (lane % LPV == 0 && k < P) s_contrib[(warp * GB + r) * PO + k] = sum;
-                }
-                if (lane == 0) s_hit[warp * NG + grp] = written;
+                for (int w = 0; w < RS; w += 4) cp_async16(dst + w, src + w);
+                cp_async4(&s_gi[st][rr], pts + q);
+                cp_async4(&s_base[st][rr], base + gi);
             }
         }
-        __syncthreads();
-        if (have) {
-            constexpr int PS = partial_stride(P);
+        cp_async_mbar_arrive_noinc(&s_mbar[st]);
+    };
+    if (warp == 0) {
+        for (uint32_t j = 0; j < (uint32_t)R && j < nb; ++j) stage(j);
+    }
+
+    uint32_t phase = 0;  // parity of the next phase to wait for, per stage
+    for (uint32_t j = 0; j < nb; ++j) {
+        const int st = (int)(j % R);
+        const uint32_t rel0 = (nb - 1 - j) * GB;
+        const uint32_t b0 = rg.x + rel0;
+        const int nrec = (int)(end - b0 < (uint32_t)GB ? end - b0 : (uint32_t)GB);
+        // Every warp waits on every phase, in order, so a parity always refers
+        // to the current or the immediately preceding phase. The lanes poll
+        // independently; the warp goes on only if all of them saw the phase.
+        if (!__all_sync(0xffffffffu, mbar_wait_or_abort(&s_mbar[st], (phase >> st) & 1u, &s_abort))) {
+            if (lane == 0) {
+                s_abort = 1u;
+                atomicOr(&hdr->error, kErrTimeout);
+            }
+            break;
+        }
+        phase ^= 1u << st;
+        const uint32_t* ring = s_ring + (size_t)st * GB * RS;
+        float* contrib = s_contrib + (size_t)(st * NW + warp) * GB * PO;
+        // (Hit words start cleared: the batch's last warp clears them.)
+#pragma unroll 1
+        for (int grp = NG - 1; grp >= 0 && wlast > rel0; --grp) {
+            const int r0 = grp * 32;
+            bool hit = false;
+            if (r0 + lane < nrec) {
+                const uint32_t* rp = ring + (r0 + lane) * RS;
+                const float um = __fsub_rn(__uint_as_float(rp[0]), 0.5f);
+                const float vm = __fsub_rn(__uint_as_float(rp[1]), 0.5f);
+                const GaussBox bx = gauss_box(um, vm, __uint_as_float(rp[7]));
+                s_box[warp][r0 + lane] = make_int4(bx.x0, bx.x1, bx.y0, bx.y1);
+                hit = bx.x0 <= sx0 + 7 && bx.x1 >= sx0 && bx.y0 <= sy0 + 3 && bx.y1 >= sy0;
+            }
+            uint32_t m = __ballot_sync(0xffffffffu, hit);
+            __syncwarp();
+            uint32_t written = 0;
+            while (m) {
+                const int bit = 31 - __clz(m);
+                m &= ~(1u << bit);
+                const int r = r0 + bit;
+                const int4 bb = s_box[warp][r];
+                bool act = inside && rel0 + r < last && px >= bb.x && px <= bb.y && py >= bb.z && py <= bb.w;
+                const uint32_t* rp = ring + r * RS;
+                float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rc = ra;
+                float dx = 0.f, dy = 0.f, mm = 0.f;
+                if (act) {
+                    const uint4 g = *reinterpret_cast<const uint4*>(rp);
+                    const uint4 h = *reinterpret_cast<const uint4*>(rp + 4);
+                    ra = make_float4(__fsub_rn(__uint_as_float(g.x), 0.5f), __fsub_rn(__uint_as_float(g.y), 0.5f),
+                                     __uint_as_float(g.w), __uint_as_float(g.z));
+                    rc = make_float4(__uint_as_float(h.x), __uint_as_float(h.y), __uint_as_float(h.z), 0.f);
+                    dx = __fsub_rn(fpx, ra.x);
+                    dy = __fsub_rn(fpy, ra.y);
+                    mm = gauss_m(dx, dy, rc.x, rc.y, rc.z);
+                    act = mm <= 9.f;
+                }
+                if (!__any_sync(0xffffffffu, act)) continue;  // no lane blended this record
+                written |= 1u << bit;
+                float v[P];
+#pragma unroll
+                for (int k = 0; k < P; ++k) v[k] = 0.f;
+                if (act) {
+                    const float G = gauss_value(mm);
+                    const float o = ra.z;
+                    const float og = __fmul_rn(o, G);
+                    const float alpha = fminf(og, amax);
+                    const float inv = rcp_fast(__fsub_rn(1.f, alpha));
+                    const float Tk = T * inv;  // T_k = T_{k+1} / (1 - alpha_k)
+                    float fr[C];
+                    load_features<C, BF16>(rp + FW, fr);
+                    float fdot = 0.f;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) fdot = fmaf(gF[c], fr[c], fdot);
+                    const float z = ra.w;
+                    const float dalpha = Tk * (fdot + gD * z) - (Sg + gD * SD + Kd) * inv;
+                    const float ta = Tk * alpha;
+                    Sg = fmaf(ta, fdot, Sg);
+                    SD = fmaf(ta, z, SD);
+                    T = Tk;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) v[c] = ta * gF[c];
+                    v[C + 6] = ta * gD;
+                    if (og <= amax) {
+                        const float dm = -0.5f * o * G * dalpha;
+                        v[C] = G * dalpha;
+                        v[C + 1] = -dm * (2.f * rc.x * dx + 2.f * rc.y * dy);
+                        v[C + 2] = -dm * (2.f * rc.y * dx + 2.f * rc.z * dy);
+                        v[C + 3] = dm * dx * dx;
+                        v[C + 4] = dm * 2.f * dx * dy;
+                        v[C + 5] = dm * dy * dy;
+                    }
+                }
+                const float sum = warp_reduce_scatter<P, 16>(v, lane);
+                if (my_k >= 0) contrib[r * PO + my_k] = sum;
+            }
+            if (lane == 0) s_hit[st][warp * NG + grp] = written;
+        }
+        // Done with the batch (its rows and hit bits written, its records read).
+        __syncwarp();
+        __threadfence_block();
+        uint32_t prev = 0;
+        if (lane == 0) prev = atomicAdd(&s_done[st], 1u);
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        if (prev != (uint32_t)(NW - 1)) continue;
+        // Last warp of the batch: a lane sums a record's rows in warp order.
+        __threadfence_block();
+#pragma unroll 1
+        for (int g = 0; g < NG; ++g) {
+            const int rr = g * 32 + lane;
+            if (rr >= nrec) continue;
             float row[PS];
 #pragma unroll
             for (int k = 0; k < PS; ++k) row[k] = 0.f;
-            const int hw = tid >> 5, hb = tid & 31;
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
-                if ((s_hit[w * NG + hw] >> hb) & 1u) {
-                    const float* cp = s_contrib + (w * GB + tid) * PO;
+                if ((s_hit[st][w * NG + g] >> lane) & 1u) {
+                    const float* cp = s_contrib + ((size_t)(st * NW + w) * GB + rr) * PO;
 #pragma unroll
                     for (int k = 0; k < P; ++k) row[k] += cp[k];
                 }
             }
-            store_row<PS>(partial + (size_t)(my_bs + (uint32_t)slot) * PS, row);
+            // The copy's rank in the point's tile rect (the projection's rect
+            // of the in-image box) picks its partial slot.
+            const uint32_t* rp = ring + rr * RS;
+            const float um = __fsub_rn(__uint_as_float(rp[0]), 0.5f);
+            const float vm = __fsub_rn(__uint_as_float(rp[1]), 0.5f);
+            const GaussBox bx = gauss_box(um, vm, __uint_as_float(rp[7]));
+            const int tx0 = max(bx.x0, 0) / TS, tx1 = min(bx.x1, V.W - 1) / TS;
+            const int ty0 = max(bx.y0, 0) / TS;
+            const int slot = (ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0);
+            store_row<PS>(partial + (size_t)(s_base[st][rr] + (uint32_t)slot) * PS, row);
+            if (b0 + rr + 1 == end) cutoff[tile] = make_uint2(rp[2], s_gi[st][rr]);
         }
-        __syncthreads();
+        __syncwarp();  // every lane has read the hit words before they are cleared
+        for (int i = lane; i < NW * NG; i += 32) s_hit[st][i] = 0;
+        if (lane == 0) s_done[st] = 0;
+        // Everything of this batch is read and the stage is clear: refill it.
+        __syncwarp();
+        __threadfence_block();
+        if (j + R < nb) stage(j + R);
     }
+    // No copy may land after the CTA has exited (only after a timeout can one
+    // still be in flight here).
+    cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------- K8 reduce
@@ -870,6 +967,22 @@ cudaError_t launch_bwd_bilinear(const ViewTable& vt, const Bufs& b, const uint32
     return cudaGetLastError();
 }
 
+template <int TS, int C, bool BF16>
+cudaError_t launch_gauss_bwd(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
+    const unsigned grid = (unsigned)vt.tiles_total;
+    constexpr size_t smem = gauss_bwd_smem<TS, C, BF16>();
+    static PerDevice attr;
+    const cudaError_t e = per_device(attr, nullptr, [](int, int*) {
+        return cudaFuncSetAttribute(k_blend_bwd_gauss<TS, C, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    });
+    if (e != cudaSuccess) return e;
+    ProfScope ps("blend_bwd", s);
+    k_blend_bwd_gauss<TS, C, BF16><<<grid, TS * TS, smem, s>>>(
+        vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.cutoff, b.hdr);
+    return cudaGetLastError();
+}
+
 template <int TS, int RPT, int C, bool BF16>
 cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts, cudaStream_t s) {
     const unsigned grid = (unsigned)vt.tiles_total;
@@ -879,16 +992,7 @@ cudaError_t launch_bwd_t(const ViewTable& vt, const Bufs& b, const uint32_t* pts
         if (b.rec_tile) return launch_bwd_bilinear<TS, RPT, C, BF16, true>(vt, b, pts, s);
         return launch_bwd_bilinear<TS, RPT, C, BF16, false>(vt, b, pts, s);
     } else {
-        constexpr size_t smem = gauss_bwd_smem<TS, C>();
-        static PerDevice attr;
-        const cudaError_t e = per_device(attr, nullptr, [](int, int*) {
-            return cudaFuncSetAttribute(k_blend_bwd_gauss<TS, C, BF16>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        });
-        if (e != cudaSuccess) return e;
-        ProfScope ps("blend_bwd", s);
-        k_blend_bwd_gauss<TS, C, BF16><<<grid, TS * TS, smem, s>>>(
-            vt, b.ranges, b.order, pts, b.rec, b.t_final, b.last, b.base, b.partial, b.cutoff, b.hdr);
+        return launch_gauss_bwd<TS, C, BF16>(vt, b, pts, s);
     }
     return cudaGetLastError();
 }
