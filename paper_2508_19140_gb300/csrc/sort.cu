@@ -12,8 +12,9 @@
 //                 per-pass tile counters and look-back status words;
 //   k_sweep       per pass, persistent CTAs take 4096-key tiles in input order
 //                 from an atomic counter, rank each key stably inside the tile
-//                 (one ballot per digit bit gives each lane the mask of lanes
-//                 holding the same digit; warps counted in ascending order),
+//                 (one ballot per digit bit, or one match instruction for
+//                 9-bit digits, gives each lane the mask of lanes holding the
+//                 same digit; warps counted in ascending order),
 //                 publish the tile's per-digit counts, and add the counts of
 //                 all earlier tiles by looking back over their published words
 //                 eight at a time (a tile whose whole prefix is known publishes
@@ -205,15 +206,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
             const int64_t idx = wbase + r * 32 + lane;
             const bool ok = idx < n;
             const uint32_t d = ok ? ((k[r] >> shift) & (BINS - 1)) : 0u;
-            // Lanes holding the same digit: one ballot per digit bit (and one
-            // for validity).
-            uint32_t peers = __ballot_sync(0xffffffffu, ok);
-            if (!ok) peers = ~peers;
+            // Lanes holding the same digit. Up to 8-bit digits: one ballot per
+            // digit bit (and one for validity); 9-bit digits: one match
+            // instruction, measured faster there (lanes past the end share a
+            // digit value of their own).
+            uint32_t peers;
+            if constexpr (BITS >= 9) {
+                peers = __match_any_sync(0xffffffffu, ok ? d : (uint32_t)BINS);
+            } else {
+                peers = __ballot_sync(0xffffffffu, ok);
+                if (!ok) peers = ~peers;
 #pragma unroll
-            for (int bb = 0; bb < BITS; ++bb) {
-                const bool set = (d >> bb) & 1u;
-                const uint32_t m = __ballot_sync(0xffffffffu, set);
-                peers &= set ? m : ~m;
+                for (int bb = 0; bb < BITS; ++bb) {
+                    const bool set = (d >> bb) & 1u;
+                    const uint32_t m = __ballot_sync(0xffffffffu, set);
+                    peers &= set ? m : ~m;
+                }
             }
             // The first lane of each digit group adds the group to the warp's
             // counter (atomics of one warp to one address apply in program
