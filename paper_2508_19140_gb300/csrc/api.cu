@@ -209,7 +209,31 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     pl.copy_cap = npt * per_pt;
     if (pl.copy_cap >= ((int64_t)1 << 30)) pl.copy_cap = ((int64_t)1 << 30) - 1;
     pl.blk_cap = (npt + kScanItems - 1) / kScanItems + 1;
-    pl.planA = make_sort_plan(bit_length(max_cull));
+    // Depth keys of a batch with several images carry the image index above
+    // the depth bits, so the depth order is image-major (views joined into
+    // one image keep one depth order). The copies of one tile all belong to
+    // one image, so the tile lists are unchanged; the duplication pass then
+    // reads each image's packed rects as a contiguous slice rather than
+    // gathering over the whole batch.
+    uint64_t key_max = max_cull;
+    {
+        const int db = bit_length(max_cull);
+        int nimg = 0;
+        for (int k = 0; k < n_views; ++k)
+            if (!(cont && cont[k] && k > 0)) ++nimg;
+        const int ib = bit_length((uint64_t)(nimg - 1));
+        if (ib > 0 && db + ib <= 32) {
+            int img = -1;
+            for (int k = 0; k < n_views; ++k) {
+                if (!(cont && cont[k] && k > 0)) ++img;
+                const uint32_t hi = (uint32_t)img << db;
+                vt.v[k].key_base -= hi;  // bits(z) - key_base = (bits(z) - bits(near)) + hi (mod 2^32)
+                vt.v[k].key_cull += hi;
+            }
+            key_max = ((uint64_t)(nimg - 1) << db) | max_cull;
+        }
+    }
+    pl.planA = make_sort_plan(bit_length(key_max));
     pl.planC = make_sort_plan(bit_length((uint64_t)(ntile > 0 ? ntile - 1 : 0)));
     pl.partial_floats = partial_stride(o->mode == RAST_SPLAT_BILINEAR ? C + 1 : C + 7);
 
