@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--graph", type=int, default=-1,
                     help="time CUDA-graph replays of the step: 1/-1 (default) = on, 0 = eager calls")
+    ap.add_argument("--batch-compare", type=int, default=-1,
+                    help="also time the 8-view BF16 batch (config 5) as one graph replay against the same "
+                         "views as sequential FP32 calls: 1 = on, 0 = off, -1 (default) = on for the "
+                         "default workload on one GPU")
     return ap.parse_args()
 
 
@@ -1049,6 +1053,22 @@ def main():
             print(json.dumps(out), flush=True)
         return
     out, dist = run_ours(args, ws_, rank, local)
+    want_batch = args.batch_compare == 1 or (args.batch_compare == -1 and args.config == 2 and
+                                             args.scale_points == 1.0)
+    if want_batch and ws_ == 1 and rank == 0:
+        # The batched-vs-sequential comparison on its own workload (8 uneven
+        # views, 62 M points, C = 8 BF16, forward + backward).
+        sub = argparse.Namespace(**vars(args))
+        sub.config, sub.steps, sub.warmup = 5, 8, 3
+        sub.tile, sub.blend_depth, sub.record_copy = 0, 0, -1
+        sub.no_e2e = sub.no_bg = sub.no_accuracy = sub.no_cpu_baseline = True
+        o5, _ = run_ours(sub, 1, 0, local)
+        bvs = dict(o5["batched_vs_sequential"] or {})
+        bvs.update({"workload": o5["config"]["workload"], "metric": o5["metric"],
+                    "batched_value": o5["value"], "unit": o5["unit"], "steps": sub.steps,
+                    "warmup": sub.warmup, "autotune": {k: (o5.get("autotune") or {}).get(k) for k in
+                                                       ("tile", "blend_depth", "record_copy")}})
+        out["batched_vs_sequential"] = bvs
     if rank == 0 and not args.no_cpu_baseline and ws_ == 1:
         from paper_2508_19140_gb300 import scenes
         import oracle
