@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
     uint32_t* s_excl = s_whist + 8 * BINS;         // BINS: tile-local digit starts
     uint32_t* s_gbase = s_excl + BINS;             // BINS: global digit starts of this tile
     uint32_t* s_goff = s_gbase + BINS;             // BINS: global digit starts of the pass
-    uint32_t* s_warp = s_goff + BINS;              // 33
+    uint32_t* s_thist = s_goff + BINS;             // BINS: the tile's digit counts
+    uint32_t* s_warp = s_thist + BINS;             // 33
     uint32_t* s_tile = s_warp + 33;                // 1
     // A pass after one whose look-back wait ran out does nothing: its input
     // is a partial order whose digit counts no longer match the histogram,
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
     // phase, so the loop spends no barrier on it. (A CTA holds the next tile
     // only while finishing one it took earlier, which never waits on it: every
     // look-back still ends.)
+    for (int i = threadIdx.x; i < BINS; i += kThreads) s_thist[i] = 0;
     if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1u);
     __syncthreads();
     for (;;) {
@@ -193,8 +195,27 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
             k[r] = ok ? kin[idx] : 0u;
             s_vin[warp * kWarpItems + r * 32 + lane] = ok ? (IDV ? (uint32_t)idx : vin[idx]) : 0u;
         }
+        // The tile's digit counts first (shared-memory adds), so they are
+        // published before the ranking: a successor's look-back then rarely
+        // finds this tile unpublished.
+#pragma unroll
+        for (int r = 0; r < kIPT; ++r)
+            if (wbase + r * 32 + lane < n) atomicAdd(&s_thist[(k[r] >> shift) & (BINS - 1)], 1u);
         for (int i = threadIdx.x; i < 8 * BINS; i += kThreads) s_whist[i] = 0;
         __syncthreads();
+        // Publish the tile's counts (test hook: with stall_test the first
+        // tile publishes nothing, so its successor's wait runs out).
+        uint32_t* my = status + tile * BINS;
+        const bool withhold = stall_test && tile == 0;
+        const uint32_t spin_limit = stall_test ? 64u : (1u << 22);
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            const int bin = threadIdx.x * VPT + q;
+            if (bin < BINS && !withhold) {
+                cuda::atomic_ref<uint32_t, cuda::thread_scope_device> w(my[bin]);
+                w.store((tile == 0 ? kFlagPrefix : kFlagAgg) | s_thist[bin], cuda::memory_order_relaxed);
+            }
+        }
 
         // Stable rank inside the warp's 512 keys: rounds in input order, lanes
         // in order within a round. Ranks (< 512) are kept two to a register.
@@ -251,20 +272,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
             }
             tot[q] = run;
         }
-        // Publish the tile's counts, then look back for the counts of all
-        // earlier tiles and publish the inclusive prefix. (Test hook: with
-        // stall_test the first tile publishes nothing, so its successor's
-        // wait runs out.)
-        uint32_t* my = status + tile * BINS;
-        const bool withhold = stall_test && tile == 0;
-        const uint32_t spin_limit = stall_test ? 64u : (1u << 22);
+        // Look back for the counts of all earlier tiles and publish the
+        // inclusive prefix.
 #pragma unroll
         for (int q = 0; q < VPT; ++q) {
             const int bin = threadIdx.x * VPT + q;
-            if (bin < BINS && !withhold) {
-                cuda::atomic_ref<uint32_t, cuda::thread_scope_device> w(my[bin]);
-                w.store((tile == 0 ? kFlagPrefix : kFlagAgg) | tot[q], cuda::memory_order_relaxed);
-            }
             if (bin < BINS) s_excl[bin] = tot[q];  // tile-local digit counts, scanned in place below
         }
         __syncthreads();
@@ -357,6 +369,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
             if (kout) kout[dst] = key;
             vout[dst] = s_vals[j];
         }
+        for (int i = threadIdx.x; i < BINS; i += kThreads) s_thist[i] = 0;  // read before the look-back barrier
         if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1u);  // every thread has read this tile's index
         __syncthreads();
     }
@@ -365,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep(
 template <int BITS>
 size_t sweep_smem() {
     constexpr int BINS = 1 << BITS;
-    return sizeof(uint32_t) * (3 * kSortTile + 8 * BINS + 3 * BINS + 33 + 1);
+    return sizeof(uint32_t) * (3 * kSortTile + 8 * BINS + 4 * BINS + 33 + 1);
 }
 
 template <int BITS>
