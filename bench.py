@@ -172,8 +172,13 @@ def kernel_bytes(name, w):
     """Algorithmic DRAM bytes of ONE launch of kernel `name` on workload counts w."""
     N, D, Dn, Db, HW, C, P = w["N"], w["D"], w["needed"], w["needed_bwd"], w["HW"], w["C"], w["P"]
     rec, fb, npart = w["rec_bytes"], w["feat_bytes"], w["partial_floats"]
-    if name == "project":   # read xyz, opacity, features; write record, key, rect, count, depth bits
-        return N * (12 + 4 + C * fb) + N * (rec + 4 + 8 + 4 + 4)
+    gauss = w.get("gauss", False)
+    rb = 8 if gauss else 4  # tile rect per point: 8 bytes (Gaussian), packed 4 bytes (bilinear)
+    if name == "project":
+        # read xyz, opacity, features (and the Gaussian scale); write the record's
+        # used words, depth key, rect (+ copy count for Gaussians) and depth bits
+        used = 4 * ((8 if gauss else 4) + -(-C * fb // 4))
+        return N * (12 + 4 + C * fb + (4 if gauss else 0)) + N * (used + 4 + rb + (4 if gauss else 0) + 4)
     if name.endswith(".hist"):      # one read of the keys counts every pass's digits
         return 4 * (N if name.startswith("depth") else D)
     if name.endswith(".sweep"):     # per pass: read key+value, write key+value
@@ -181,10 +186,10 @@ def kernel_bytes(name, w):
             passes = max(w.get("depth_passes", 1), 1)
             return (16 * passes - 4) * N / passes
         return 16 * D
-    if name == "dup.count":
-        return N * (4 + 8 + 8)
+    if name == "dup.count":   # sorted point indices, gathered rects, rects in depth order
+        return N * (4 + rb + rb)
     if name == "dup.write":
-        return N * (8 + 4) + D * 8
+        return N * (rb + 4) + D * 8
     if name == "ranges":
         return D * 4 + P * 8
     if name == "blend_fwd":
@@ -196,7 +201,7 @@ def kernel_bytes(name, w):
     if name == "blend_bwd":   # replayed records + indices, one gradient row per copy, pixel state
         return Db * (rec + 4 + 4 * npart) + P * 16 + HW * (4 * C + 16)
     if name == "reduce_grads":
-        return N * (8 + 4 + 4) + Db * 4 * npart + N * (4 * C + 4)
+        return N * (rb + 4 + 4) + Db * 4 * npart + N * (4 * C + 4)
     return 0
 
 
@@ -429,7 +434,7 @@ def run_ours(args, ws_, rank, local):
              needed_bwd=int(stats["needed_records_bwd"]),
              HW=sum(v.camera.width * v.camera.height for v in scene.views), C=C,
              P=int(stats["n_tiles"]), rec_bytes=rec_bytes, feat_bytes=2 if bf16 else 4,
-             partial_floats=C + (7 if gauss else 1),
+             partial_floats=C + (7 if gauss else 1), gauss=gauss,
              depth_passes=int(round(prof.get("depth_sort.sweep", (0, 0))[0] / max(prof.get("init_header", (1, 0))[0], 1))))
     peak, peak_src = measured_peak_hbm()
     kernels = {}
