@@ -187,6 +187,13 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* __restrict__ blk
 constexpr int kTW = 2 * kT;
 constexpr int kPerW = kScanItems / kTW;
 static_assert(kPerW == 4, "the packed-rect path loads four rects as one 16-byte vector");
+// Gaussian copies a block stages in shared memory before writing them out
+// (four a point on average fit; a block with more writes its copies
+// directly). Bilinear points make at most four copies each, in runs of one
+// to four per thread, and write them directly: measured, staging them costs
+// more occupancy than the scattered stores do.
+constexpr int kStageCap = 4 * kScanItems;
+constexpr size_t kDupWriteSmem = sizeof(uint32_t) * 2 * kStageCap;
 
 template <bool P4>
 __global__ void __launch_bounds__(kTW) k_dup_write(const ViewTable vt, const uint32_t* __restrict__ sorted_pts,
@@ -195,6 +202,7 @@ __global__ void __launch_bounds__(kTW) k_dup_write(const ViewTable vt, const uin
                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                    int64_t cap) {
     __shared__ uint32_t s_warp[33];
+    extern __shared__ uint32_t s_copy[];  // [kStageCap] tile ids, then [kStageCap] point indices
     const int64_t s0 = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kPerW;
     uint2 r[kPerW];
     uint32_t gi[kPerW];
@@ -232,7 +240,13 @@ __global__ void __launch_bounds__(kTW) k_dup_write(const ViewTable vt, const uin
         sum += c[j];
     }
     uint32_t tot;
-    uint32_t o = blk[blockIdx.x] + block_excl_scan<kTW>(sum, s_warp, tot);
+    const uint32_t ex = block_excl_scan<kTW>(sum, s_warp, tot);
+    const uint32_t blk0 = blk[blockIdx.x];
+    // The block's copies fill one contiguous range of the output: staged in
+    // shared memory, they leave in coalesced runs instead of one scattered
+    // 4-byte store per copy and array.
+    const bool staged = !P4 && tot <= (uint32_t)kStageCap;
+    uint32_t o = staged ? ex : blk0 + ex;
 #pragma unroll
     for (int j = 0; j < kPerW; ++j) {
         if (c[j] == 0) continue;
@@ -241,12 +255,24 @@ __global__ void __launch_bounds__(kTW) k_dup_write(const ViewTable vt, const uin
         for (int ty = ty0; ty <= ty1; ++ty) {
             const uint32_t row = (uint32_t)(V.tile_off + (int64_t)ty * V.tiles_x);
             for (int tx = tx0; tx <= tx1; ++tx) {
-                if ((int64_t)o < cap) {
+                if (staged) {
+                    s_copy[o] = row + (uint32_t)tx;
+                    s_copy[kStageCap + o] = gi[j];
+                } else if ((int64_t)o < cap) {
                     keys[o] = row + (uint32_t)tx;
                     vals[o] = gi[j];
                 }
                 ++o;
             }
+        }
+    }
+    if (!staged) return;  // block-uniform
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < tot; i += kTW) {
+        const int64_t g = (int64_t)blk0 + i;
+        if (g < cap) {
+            keys[g] = s_copy[i];
+            vals[g] = s_copy[kStageCap + i];
         }
     }
 }
@@ -412,13 +438,19 @@ cudaError_t launch_duplicate(const ViewTable& vt, const Bufs& b, const uint32_t*
         k_scan_blocks<<<1, 1024, 0, s>>>(b.blk, nb, b.hdr, b.copy_cap);
     }
     {
+        static PerDevice attr;
+        const cudaError_t e = per_device(attr, nullptr, [](int, int*) {
+            return cudaFuncSetAttribute(k_dup_write<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kDupWriteSmem);
+        });
+        if (e != cudaSuccess) return e;
         ProfScope ps("dup.write", s);
         if (vt.mode == 0)
             k_dup_write<true><<<(unsigned)nb, kTW, 0, s>>>(vt, sorted_pts, b.rect4S, n, b.blk, b.keyC[0],
                                                          b.valC[0], b.copy_cap);
         else
-            k_dup_write<false><<<(unsigned)nb, kTW, 0, s>>>(vt, sorted_pts, b.rectS, n, b.blk, b.keyC[0],
-                                                          b.valC[0], b.copy_cap);
+            k_dup_write<false><<<(unsigned)nb, kTW, kDupWriteSmem, s>>>(vt, sorted_pts, b.rectS, n, b.blk,
+                                                                      b.keyC[0], b.valC[0], b.copy_cap);
     }
     return cudaGetLastError();
 }
