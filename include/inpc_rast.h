@@ -92,7 +92,8 @@ typedef struct {
     float alpha_max;       /* alpha clamp (0.99) */
     float dilation;        /* screen-space dilation variance, Gaussian mode (0.16) */
     int32_t max_copies;    /* capacity: point-tile copies per point (0 = 4 bilinear, 16 Gaussian) */
-    int32_t flags;         /* 0 or an OR of RAST_FLAG_SAVE_FOR_BWD and RAST_FLAG_TEST_SORT_STALL */
+    int32_t flags;         /* 0 or an OR of RAST_FLAG_SAVE_FOR_BWD, RAST_FLAG_TEST_SORT_STALL and
+                              RAST_FLAG_TEST_BLEND_STALL */
 } rast_opts_t;
 
 /* The forward blend also writes a copy of every point record it reads, in
@@ -115,6 +116,16 @@ typedef struct {
  * rasterize_get_status() returns RAST_ERR_TIMEOUT. Needs more than 4096
  * points. Never set outside tests. */
 #define RAST_FLAG_TEST_SORT_STALL 1
+
+/* Test hook for the bounded waits of the Gaussian backward blend (failure
+ * detection). With this flag in the opts of a Gaussian backward pass, the
+ * second batch of every tile with more than 32 replayed records is never
+ * staged, so the warps' waits on its staging barrier can never succeed, and
+ * each wait is limited to 64 polls instead of 2^20. The waits run out, the
+ * kernel sets the timeout bit of the workspace error word and returns
+ * normally (the point gradients are then incomplete), and
+ * rasterize_get_status() returns RAST_ERR_TIMEOUT. Never set outside tests. */
+#define RAST_FLAG_TEST_BLEND_STALL 4
 
 typedef struct {
     float* feat;    /* [H][W][C] out */

@@ -111,7 +111,8 @@ rast_status_t make_plan(const rast_view_t* views, int32_t n_views, const rast_op
     if (!untiled && !blend_depth_supported(o->mode, o->tile, depth)) return RAST_ERR_NOT_SUPPORTED;
     if (!(o->t_min >= 0.f) || !(o->alpha_max > 0.f && o->alpha_max < 1.f)) return RAST_ERR_ARG;
     if (!(o->dilation >= 0.f) || o->max_copies < 0) return RAST_ERR_ARG;
-    if ((o->flags & ~(RAST_FLAG_TEST_SORT_STALL | RAST_FLAG_SAVE_FOR_BWD)) != 0) return RAST_ERR_ARG;
+    if ((o->flags & ~(RAST_FLAG_TEST_SORT_STALL | RAST_FLAG_SAVE_FOR_BWD | RAST_FLAG_TEST_BLEND_STALL)) != 0)
+        return RAST_ERR_ARG;
     const int C = views[0].pts.channels;
     const int dt = views[0].pts.feat_dtype;
     if (dt != RAST_F32 && dt != RAST_BF16) return RAST_ERR_ARG;

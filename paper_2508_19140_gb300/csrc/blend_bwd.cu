@@ -481,11 +481,12 @@ constexpr size_t gauss_bwd_smem() {
            sizeof(float) * kGaussStages * (TS * TS / 32) * kGaussBatch * gauss_contrib_stride(C + 7);
 }
 
-// Polls `bar` for the phase of this parity, giving up after kMbarPolls polls
-// or once another warp of the CTA has given up (abort flag).
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const volatile uint32_t* abort) {
+// Polls `bar` for the phase of this parity, giving up after `polls` polls or
+// once another warp of the CTA has given up (abort flag).
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const volatile uint32_t* abort,
+                                                   uint32_t polls) {
     const uint32_t b = smem_addr(bar);
-    for (uint32_t i = 0; i < kMbarPolls; ++i) {
+    for (uint32_t i = 0; i < polls; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -595,11 +596,16 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     const uint32_t nb = (maxlast - 1) / GB + 1;  // batches; iteration j handles batch nb - 1 - j
     const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
     const int my_k = scatter_index<P, 16>(lane);  // the warp sum this lane writes, if any
+    // Test hook (RAST_FLAG_TEST_BLEND_STALL): iteration 1 is never staged and
+    // every wait gives up after 64 polls.
+    const bool stall_test = (vt.flags & RAST_FLAG_TEST_BLEND_STALL) != 0;
+    const uint32_t polls = stall_test ? 64u : kMbarPolls;
 
     // Stages iteration j (all 32 lanes of one warp): lane l copies record l of
     // the batch, its point index and its partial-slot base, then arrives on
     // the stage's barrier once its copies have landed.
     auto stage = [&](uint32_t j) {
+        if (stall_test && j == 1) return;  // nothing arrives: the waits on this phase run out
         const int st = (int)(j % R);
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
@@ -630,7 +636,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
         // Every warp waits on every phase, in order, so a parity always refers
         // to the current or the immediately preceding phase. The lanes poll
         // independently; the warp goes on only if all of them saw the phase.
-        if (!__all_sync(0xffffffffu, mbar_wait_or_abort(&s_mbar[st], (phase >> st) & 1u, &s_abort))) {
+        if (!__all_sync(0xffffffffu, mbar_wait_or_abort(&s_mbar[st], (phase >> st) & 1u, &s_abort, polls))) {
             if (lane == 0) {
                 s_abort = 1u;
                 atomicOr(&hdr->error, kErrTimeout);

@@ -33,6 +33,7 @@ F32, BF16 = 0, 1
 PASS_FWD, PASS_BWD = 1, 2
 FLAG_TEST_SORT_STALL = 1  # RAST_FLAG_TEST_SORT_STALL: failure-path tests only
 FLAG_SAVE_FOR_BWD = 2     # RAST_FLAG_SAVE_FOR_BWD: the forward keeps a tile-ordered record copy for the backward
+FLAG_TEST_BLEND_STALL = 4  # RAST_FLAG_TEST_BLEND_STALL: failure-path tests only
 
 
 class RastError(RuntimeError):

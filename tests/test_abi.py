@@ -129,7 +129,7 @@ def test_argument_validation_is_synchronous(lib):
             rast.RAST_ERR_NOT_SUPPORTED, (t, d, m)
     assert B(arr, 1, 1, ct.byref(_opts(lib, mode=7)), ws, big, None) == rast.RAST_ERR_ARG
     assert B(arr, 1, 1, ct.byref(_opts(lib, alpha_max=1.0)), ws, big, None) == rast.RAST_ERR_ARG
-    assert B(arr, 1, 1, ct.byref(_opts(lib, flags=4)), ws, big, None) == rast.RAST_ERR_ARG  # unknown flag
+    assert B(arr, 1, 1, ct.byref(_opts(lib, flags=8)), ws, big, None) == rast.RAST_ERR_ARG  # unknown flag
     assert B(arr, 1, 1, ct.byref(o), None, big, None) == rast.RAST_ERR_ARG
     assert B(arr, 1, 1, ct.byref(o), ct.c_void_p((1 << 20) + 4), big, None) == rast.RAST_ERR_ARG
     assert B(arr, 1, 1, ct.byref(o), ws, 1024, None) == rast.RAST_ERR_CAPACITY

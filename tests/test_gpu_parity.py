@@ -442,6 +442,29 @@ def test_bounded_wait_runs_out_and_is_reported():
     _check_image(ok, ref)
 
 
+def test_gauss_backward_bounded_wait_runs_out_and_is_reported():
+    """Failure detection without a fault, Gaussian backward: with the test
+    hook the second batch of every tile with more than 32 replayed records is
+    never staged, so the warps' waits on its barrier (64 polls under the hook)
+    run out. The call must return and report RAST_ERR_TIMEOUT, the forward
+    before it must be untouched, and the context must stay usable: a normal
+    forward + backward afterwards gives the same bits as one before."""
+    from paper_2508_19140_gb300 import rast
+    v = case_view("gauss")
+    before = Run([v], mode="gaussian", backward=True)
+    assert rast.rasterize_get_status(before.ws)[0] == 0
+    r = Run([v], mode="gaussian", backward=True, flags=rast.FLAG_TEST_BLEND_STALL, ws_fill=0xFF)
+    assert r.status == 0  # the forward ignores the hook
+    assert rast.rasterize_get_status(r.ws)[0] == rast.RAST_ERR_TIMEOUT
+    for a, b in zip(r.image(), before.image()):
+        assert np.array_equal(a, b)
+    after = Run([v], mode="gaussian", backward=True)
+    assert rast.rasterize_get_status(after.ws)[0] == 0
+    g0, g1 = before.grads(), after.grads()
+    for key in g0:
+        assert np.array_equal(g0[key], g1[key]), key
+
+
 def test_wide_depth_range_uses_widest_digits():
     """near 1e-4, far 1e8: depth keys bits(z) - bits(near) of 29 bits, which the
     split sort covers with its widest digits (four 8-bit passes)."""
