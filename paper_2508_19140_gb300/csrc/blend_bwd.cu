@@ -541,6 +541,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     float* const s_contrib = reinterpret_cast<float*>(s_ring + R * GB * RS);      // [R][NW][GB][PO]
     __shared__ uint32_t s_gi[R][GB];               // point index of each staged record
     __shared__ uint32_t s_base[R][GB];             // its first partial slot
+    __shared__ uint32_t s_pnext[R][GB];            // point indices of the batch a stage takes next
     __shared__ uint32_t s_hit[R][NW * NG];         // records each warp contributed to
     __shared__ uint32_t s_done[R];                 // warps done with the stage's batch
     __shared__ __align__(8) uint64_t s_mbar[R];    // stage filled (32 arrivals: the staging lanes)
@@ -604,6 +605,8 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
     // Stages iteration j (all 32 lanes of one warp): lane l copies record l of
     // the batch, its point index and its partial-slot base, then arrives on
     // the stage's barrier once its copies have landed.
+    // Iterations j >= R take their point indices from s_pnext (loaded by one
+    // warp while it worked on iteration j - R, off the staging warp's path).
     auto stage = [&](uint32_t j) {
         if (stall_test && j == 1) return;  // nothing arrives: the waits on this phase run out
         const int st = (int)(j % R);
@@ -612,7 +615,7 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
             const int rr = g * 32 + lane;
             const uint32_t q = rg.x + (nb - 1 - j) * GB + rr;
             if (q < end) {
-                const uint32_t gi = pts[q];
+                const uint32_t gi = j < (uint32_t)R ? pts[q] : s_pnext[st][rr];
                 uint32_t* dst = s_ring + ((size_t)st * GB + rr) * RS;
                 const uint32_t* src = rec + (size_t)gi * RW;
 #pragma unroll
@@ -644,6 +647,18 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
             break;
         }
         phase ^= 1u << st;
+        // One warp per iteration loads the point indices of iteration j + R
+        // now and stores them before it counts itself done, so the load's
+        // latency overlaps its own work on this batch.
+        const bool pref = warp == (int)(j % NW) && j + R < nb;
+        uint32_t pnext[NG];
+        if (pref) {
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const uint32_t q = rg.x + (nb - 1 - (j + R)) * GB + g * 32 + lane;
+                pnext[g] = q < end ? pts[q] : 0u;
+            }
+        }
         const uint32_t* ring = s_ring + (size_t)st * GB * RS;
         float* contrib = s_contrib + (size_t)(st * NW + warp) * GB * PO;
         // (Hit words start cleared: the batch's last warp clears them.)
@@ -722,6 +737,10 @@ __global__ void __launch_bounds__(TS * TS) k_blend_bwd_gauss(
                 if (my_k >= 0) contrib[r * PO + my_k] = sum;
             }
             if (lane == 0) s_hit[st][warp * NG + grp] = written;
+        }
+        if (pref) {
+#pragma unroll
+            for (int g = 0; g < NG; ++g) s_pnext[st][g * 32 + lane] = pnext[g];
         }
         // Done with the batch (its rows and hit bits written, its records read).
         __syncwarp();
