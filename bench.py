@@ -162,8 +162,8 @@ MEASURED_TRAFFIC = {
     ("blend_fwd", 2, 8, 64, 1): 528297216,
     ("blend_bwd", 2, 8, 64, 1): 412425216,
     ("blend_fwd", 3, 16, 256, 0): 2890925056,
-    ("blend_fwd", 4, 16, 256, 0): 383619584,
-    ("blend_bwd", 4, 16, 256, 0): 1149000960,
+    ("blend_fwd", 4, 16, 256, 0): 380597760,
+    ("blend_bwd", 4, 16, 256, 0): 1149237248,
     ("blend_fwd", 5, 8, 64, 1): 9635505408,
     ("blend_bwd", 5, 8, 64, 1): 9302492928,
 }
