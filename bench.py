@@ -201,7 +201,9 @@ def kernel_bytes(name, w):
     if name == "blend_bwd":   # replayed records + indices, one gradient row per copy, pixel state
         return Db * (rec + 4 + 4 * npart) + P * 16 + HW * (4 * C + 16)
     if name == "reduce_grads":
-        return N * (rb + 4 + 4) + Db * 4 * npart + N * (4 * C + 4)
+        # rect, depth bits, slot base; the rows; dL/df and dL/do; Gaussians also
+        # read the position and scale and write dL/dxyz and dL/ds
+        return N * (rb + 4 + 4) + Db * 4 * npart + N * (4 * C + 4) + (N * (12 + 4 + 12 + 4) if gauss else 0)
     return 0
 
 
